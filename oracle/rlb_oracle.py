@@ -1,0 +1,369 @@
+"""Plain FP64 CPU oracle of the relativistic lattice Boltzmann (RLB) scheme.
+
+TEST INFRASTRUCTURE ONLY.  This module is the slow, obviously-correct statement of
+what the GPU library computes.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference leg of ``bench.py`` may import it.  The product path (the
+CUDA library ``librlb`` and its Python binding) never imports, calls or links it,
+and this module imports nothing from the product package.
+
+Source: Q. Li, K. H. Luo, X. J. Li, "Lattice Boltzmann method for relativistic
+hydrodynamics: issues on conservation law of particle number and discontinuities"
+(arXiv 1211.3286).  Every function cites the equation it follows.  Arithmetic is
+FP64 (or complex128 for complex-step derivatives) with plain PyTorch CPU tensor ops;
+the 19x19 MRT transform uses an explicit matrix and ``torch.linalg.inv`` as its
+library primitives.  There is no blocking, fusion or reordering beyond the
+per-node definitions.
+
+Readings of the paper taken here (the paper is silent or D2Q9-only on these):
+  * D3Q19 velocity set and weights are not printed next to Eq. 7; the standard set
+    is used: rest, 6 axis links (w=1/18), 12 face diagonals (w=1/36), c_s^2 = 1/3
+    (the c_s = c/sqrt(3) stated after Eq. 10).  Ordering: 0 rest; 1..6 = +x,-x,+y,
+    -y,+z,-z; 7..18 = (+1,+1,0),(-1,-1,0),(+1,-1,0),(-1,+1,0),(+1,0,+1),(-1,0,-1),
+    (+1,0,-1),(-1,0,+1),(0,+1,+1),(0,-1,-1),(0,+1,-1),(0,-1,+1), so that the
+    opposite of link a (odd) is a+1.
+  * Equation of state P = e/3 (ultrarelativistic ideal fluid, consistent with
+    c_s^2 = 1/3).
+  * Eq. 10 gives the moments, not their inverse.  With P = e/3,
+    sigma = (e+P) gamma^2 = 4 e gamma^2 / 3, T00 = sigma - P and M = sigma u, so
+    |M| u^2 - 4 T00 |u| + 3 |M| = 0; the physical root (|u| < 1) is written in the
+    cancellation-free vector form u = 3 M / (2 T00 + sqrt(4 T00^2 - 3 M.M)), then
+    sigma = 4 T00 / (3 + u^2), e = 3 (sigma - T00), P = e / 3,
+    gamma = 1/sqrt(1-u^2), n = N0 / gamma.
+  * The paper's MRT (Eqs. 30-35) is D2Q9 with the matrix taken from its Ref. [24].
+    For D3Q19 the moment basis of d'Humieres et al. (Phil. Trans. R. Soc. A 360,
+    437 (2002)) is used.  Rates: density and momentum (conserved) relax with 1
+    (tau_sigma = tau_j = delta_t, as under Eq. 31), energy e with 1/tau_e, energy
+    square epsilon with 1/tau_eps, energy flux q with 1/tau_q, every other moment
+    (shear p, pi, m) with 1/tau_v.
+  * f always relaxes by BGK (Eq. 5) with its own tau_f; MRT replaces only Eq. 6.
+  * "Open" ends are zero-gradient: a pull from outside [0, L) takes the edge
+    node's post-collision population of the same link.
+  * The initial state is f = f^eq, g = g^eq of the initial fields.  The state after
+    step t is the post-collision lattice; the fields reported at t are Eq. 10 plus
+    the recovery applied to that stored lattice.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Sequence
+
+import torch
+
+DT = torch.float64
+CS2 = 1.0 / 3.0  # c_s^2, c_s = c/sqrt(3) with c = 1 (stated after Eq. 10)
+
+PERIODIC = "periodic"
+ZERO_GRADIENT = "zero_gradient"
+
+
+# ----------------------------------------------------------------------------- lattice
+def d3q19():
+    """D3Q19 velocity set e_alpha (19x3, integer) and weights w_alpha (19).
+
+    The lattice is the one named before Eq. 7; its table is the standard one (not
+    printed in the paper).  Returned as FP64 tensors (velocities are exact small
+    integers)."""
+    links = [(0, 0, 0),
+             (1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1),
+             (1, 1, 0), (-1, -1, 0), (1, -1, 0), (-1, 1, 0),
+             (1, 0, 1), (-1, 0, -1), (1, 0, -1), (-1, 0, 1),
+             (0, 1, 1), (0, -1, -1), (0, 1, -1), (0, -1, 1)]
+    E = torch.tensor(links, dtype=DT)
+    W = torch.empty(19, dtype=DT)
+    for a, c in enumerate(links):
+        c2 = sum(x * x for x in c)
+        W[a] = {0: 1.0 / 3.0, 1: 1.0 / 18.0, 2: 1.0 / 36.0}[c2]
+    return E, W
+
+
+def opposite():
+    """Index of the link opposite to each link (e_opp = -e)."""
+    E, _ = d3q19()
+    opp = []
+    for a in range(19):
+        for b in range(19):
+            if torch.equal(E[b], -E[a]):
+                opp.append(b)
+                break
+    return opp
+
+
+def _edotu(E, u):
+    """e_alpha . u for every link: (19, *grid) from u of shape (3, *grid)."""
+    return torch.einsum("ai,i...->a...", E.to(u.dtype), u)
+
+
+def _bcast(w, like):
+    """Reshape a per-link vector (19,) to broadcast against (19, *grid)."""
+    return w.to(like.dtype).reshape((19,) + (1,) * (like.dim() - 1))
+
+
+# ----------------------------------------------------------------------------- equilibria
+def f_eq(n, u):
+    """Number equilibrium, Eq. 7:
+    f^eq_a = w_a n gamma [1 + e.u/c_s^2 + (e.u)^2/(2 c_s^4) - u^2/(2 c_s^2)]."""
+    E, W = d3q19()
+    u2 = (u * u).sum(0)
+    gamma = 1.0 / torch.sqrt(1.0 - u2)
+    eu = _edotu(E, u)
+    return _bcast(W, eu) * (n * gamma) * (1.0 + eu / CS2 + eu * eu / (2.0 * CS2 * CS2) - u2 / (2.0 * CS2))
+
+
+def g_eq(e, P, u):
+    """Energy-momentum equilibrium, Eqs. 8 (rest link) and 9 (moving links), with
+    sigma = (e + P) gamma^2."""
+    E, W = d3q19()
+    u2 = (u * u).sum(0)
+    gamma2 = 1.0 / (1.0 - u2)
+    sigma = (e + P) * gamma2
+    eu = _edotu(E, u)
+    Wb = _bcast(W, eu)
+    moving = Wb * sigma * (P / (sigma * CS2) + eu / CS2 + eu * eu / (2.0 * CS2 * CS2) - u2 / (2.0 * CS2))
+    rest = W[0] * sigma * (3.0 - P * (2.0 + 3.0 * CS2) / (sigma * CS2) - u2 / (2.0 * CS2))
+    out = moving.clone()
+    out[0] = rest
+    return out
+
+
+# ----------------------------------------------------------------------------- moments / recovery
+def moments(f, g):
+    """Eq. 10: N0 = n gamma = sum_a f_a, T00 = (e+P) gamma^2 - P = sum_a g_a,
+    M = (e+P) gamma^2 u = sum_a e_a g_a.  Sums run over links in index order."""
+    E, _ = d3q19()
+    N0 = f[0].clone()
+    T00 = g[0].clone()
+    M = torch.zeros((3,) + tuple(g.shape[1:]), dtype=g.dtype)
+    for a in range(1, 19):
+        N0 = N0 + f[a]
+        T00 = T00 + g[a]
+    for a in range(19):
+        for i in range(3):
+            if E[a, i] != 0:
+                M[i] = M[i] + E[a, i].item() * g[a]
+    return N0, T00, M
+
+
+@dataclasses.dataclass
+class Fields:
+    e: torch.Tensor
+    P: torch.Tensor
+    u: torch.Tensor      # (3, *grid)
+    gamma: torch.Tensor
+    n: torch.Tensor
+    sigma: torch.Tensor
+
+
+class NonPhysical(ValueError):
+    pass
+
+
+def recover(N0, T00, M, check: bool = True) -> Fields:
+    """Invert Eq. 10 under P = e/3 (closed form, no iteration):
+    u = 3 M / (2 T00 + sqrt(4 T00^2 - 3 M.M)),  sigma = 4 T00 / (3 + u^2),
+    e = 3 (sigma - T00),  P = e / 3,  gamma = 1 / sqrt(1 - u^2),  n = N0 / gamma
+    (the velocity comes from g, as stated in Sec. III.A)."""
+    MM = (M * M).sum(0)
+    disc = 4.0 * T00 * T00 - 3.0 * MM
+    if check and not torch.is_complex(disc):
+        bad = (disc < 0) | (T00 <= 0) | torch.isnan(disc)
+        if bool(bad.any()):
+            raise NonPhysical("4 T00^2 - 3 |M|^2 < 0 or T00 <= 0 at %d nodes" % int(bad.sum()))
+    u = 3.0 * M / (2.0 * T00 + torch.sqrt(disc))
+    u2 = (u * u).sum(0)
+    sigma = 4.0 * T00 / (3.0 + u2)
+    e = 3.0 * (sigma - T00)
+    P = e / 3.0
+    gamma = 1.0 / torch.sqrt(1.0 - u2)
+    n = N0 / gamma
+    if check and not torch.is_complex(e):
+        bad = (e <= 0) | (u2 >= 1.0) | torch.isnan(e)
+        if bool(bad.any()):
+            raise NonPhysical("e <= 0 or |u| >= 1 at %d nodes" % int(bad.sum()))
+    return Fields(e=e, P=P, u=u, gamma=gamma, n=n, sigma=sigma)
+
+
+# ----------------------------------------------------------------------------- MRT
+MRT_ROWS = ["rho", "e", "eps", "jx", "qx", "jy", "qy", "jz", "qz",
+            "pxx", "pixx", "pww", "piww", "pxy", "pyz", "pxz", "mx", "my", "mz"]
+
+
+def mrt_matrix():
+    """19x19 moment matrix M of the D3Q19 MRT model (rows are polynomials of the
+    link velocity c, after d'Humieres et al. 2002), replacing the D2Q9 matrix that
+    Eqs. 30-35 take from the paper's Ref. [24]:
+      rho = 1, e = 19|c|^2 - 30, eps = (21|c|^4 - 53|c|^2 + 24)/2, j_i = c_i,
+      q_i = (5|c|^2 - 9) c_i, p_xx = 3c_x^2 - |c|^2, pi_xx = (3|c|^2 - 5) p_xx,
+      p_ww = c_y^2 - c_z^2, pi_ww = (3|c|^2 - 5) p_ww, p_xy = c_x c_y,
+      p_yz = c_y c_z, p_xz = c_x c_z, m_x = (c_y^2 - c_z^2) c_x,
+      m_y = (c_z^2 - c_x^2) c_y, m_z = (c_x^2 - c_y^2) c_z."""
+    E, _ = d3q19()
+    Mx = torch.zeros(19, 19, dtype=DT)
+    for a in range(19):
+        cx, cy, cz = (E[a, 0].item(), E[a, 1].item(), E[a, 2].item())
+        c2 = cx * cx + cy * cy + cz * cz
+        row = {
+            "rho": 1.0,
+            "e": 19.0 * c2 - 30.0,
+            "eps": (21.0 * c2 * c2 - 53.0 * c2 + 24.0) / 2.0,
+            "jx": cx, "qx": (5.0 * c2 - 9.0) * cx,
+            "jy": cy, "qy": (5.0 * c2 - 9.0) * cy,
+            "jz": cz, "qz": (5.0 * c2 - 9.0) * cz,
+            "pxx": 3.0 * cx * cx - c2,
+            "pixx": (3.0 * c2 - 5.0) * (3.0 * cx * cx - c2),
+            "pww": cy * cy - cz * cz,
+            "piww": (3.0 * c2 - 5.0) * (cy * cy - cz * cz),
+            "pxy": cx * cy, "pyz": cy * cz, "pxz": cx * cz,
+            "mx": (cy * cy - cz * cz) * cx,
+            "my": (cz * cz - cx * cx) * cy,
+            "mz": (cx * cx - cy * cy) * cz,
+        }
+        for k, name in enumerate(MRT_ROWS):
+            Mx[k, a] = row[name]
+    return Mx
+
+
+def relaxation_diag(tau_v, tau_e, tau_eps, tau_q, like=None):
+    """Diagonal of S (the D3Q19 analogue of Eq. 31): conserved rho, j -> 1;
+    e -> 1/tau_e; eps -> 1/tau_eps; q -> 1/tau_q; p, pi, m -> 1/tau_v.
+    Arguments may be Python floats or 0-d tensors (for autograd / complex step)."""
+    def t(x):
+        return x if torch.is_tensor(x) else torch.tensor(float(x), dtype=DT)
+    tv, te, tq, tp = t(tau_v), t(tau_e), t(tau_q), t(tau_eps)
+    one = torch.ones((), dtype=tv.dtype)
+    rate = {"rho": one, "jx": one, "jy": one, "jz": one,
+            "e": 1.0 / te, "eps": 1.0 / tp, "qx": 1.0 / tq, "qy": 1.0 / tq, "qz": 1.0 / tq}
+    return torch.stack([rate.get(name, 1.0 / tv) * one for name in MRT_ROWS])
+
+
+# ----------------------------------------------------------------------------- collision
+def collide_bgk(p, peq, tau):
+    """BGK relaxation, Eqs. 5 and 6 with delta_t = 1: p* = p - (p - p^eq)/tau."""
+    return p - (p - peq) / tau
+
+
+def collide_mrt(g, geq, S):
+    """MRT relaxation of g, Eqs. 30 and 35 with delta_t = 1:
+    m = M g, m^eq = M g^eq, m* = m - S (m - m^eq), g* = M^{-1} m*."""
+    Mx = mrt_matrix().to(g.dtype)
+    Minv = torch.linalg.inv(mrt_matrix()).to(g.dtype)
+    shape = g.shape
+    m = Mx @ g.reshape(19, -1)
+    meq = Mx @ geq.reshape(19, -1)
+    mstar = m - S.to(g.dtype).reshape(19, 1) * (m - meq)
+    return (Minv @ mstar).reshape(shape)
+
+
+# ----------------------------------------------------------------------------- streaming
+def _source_index(n, c, bc):
+    idx = torch.arange(n) - int(c)
+    if bc == PERIODIC:
+        return torch.remainder(idx, n)
+    if bc == ZERO_GRADIENT:
+        return idx.clamp(0, n - 1)
+    raise ValueError(bc)
+
+
+def stream_pull(pop, bc: Sequence[str]):
+    """Pull streaming (left-hand sides of Eqs. 5, 6, 30): the population of link a
+    arriving at node x is the post-collision one at x - e_a.  ``pop`` is laid out
+    (19, nz, ny, nx); ``bc`` gives (bc_x, bc_y, bc_z).  Periodic axes wrap,
+    zero-gradient axes clamp the source node into the domain."""
+    E, _ = d3q19()
+    _, nz, ny, nx = pop.shape
+    out = torch.empty_like(pop)
+    for a in range(19):
+        cx, cy, cz = (int(E[a, 0]), int(E[a, 1]), int(E[a, 2]))
+        sx = _source_index(nx, cx, bc[0])
+        sy = _source_index(ny, cy, bc[1])
+        sz = _source_index(nz, cz, bc[2])
+        out[a] = pop[a][sz][:, sy][:, :, sx]
+    return out
+
+
+# ----------------------------------------------------------------------------- the scheme
+@dataclasses.dataclass
+class Params:
+    collision: str = "mrt"              # "bgk" or "mrt" (g); f is always BGK
+    tau_f: float = 0.9
+    tau_v: float = 0.9                  # BGK uses tau_v for g
+    tau_e: float = 0.9
+    tau_eps: float = 0.9
+    tau_q: float = 0.0                  # <= 0 means tau_q = tau_v
+    bc: tuple = (PERIODIC, PERIODIC, PERIODIC)
+
+    def tq(self):
+        return self.tau_v if (not torch.is_tensor(self.tau_q) and self.tau_q <= 0) else self.tau_q
+
+
+def init_populations(e, u, n):
+    """Initial state: f = f^eq(n, u), g = g^eq(e, P = e/3, u) (Eqs. 7-9)."""
+    return f_eq(n, u), g_eq(e, e / 3.0, u)
+
+
+def collide(f, g, prm: Params, check: bool = True):
+    """Moments (Eq. 10) -> recovery -> equilibria (Eqs. 7-9) -> relaxation
+    (Eq. 5 for f; Eq. 6 or Eqs. 30/35 for g) at every node."""
+    N0, T00, M = moments(f, g)
+    fl = recover(N0, T00, M, check=check)
+    feq = f_eq(fl.n, fl.u)
+    geq = g_eq(fl.e, fl.P, fl.u)
+    fs = collide_bgk(f, feq, prm.tau_f)
+    if prm.collision == "bgk":
+        gs = collide_bgk(g, geq, prm.tau_v)
+    elif prm.collision == "mrt":
+        S = relaxation_diag(prm.tau_v, prm.tau_e, prm.tau_eps, prm.tq())
+        gs = collide_mrt(g, geq, S)
+    else:
+        raise ValueError(prm.collision)
+    return fs, gs
+
+
+def step(f, g, prm: Params, check: bool = True):
+    """One time step: pull-stream the post-collision lattice, then collide."""
+    return collide(stream_pull(f, prm.bc), stream_pull(g, prm.bc), prm, check=check)
+
+
+def run(f, g, prm: Params, nsteps: int, check: bool = True):
+    for _ in range(nsteps):
+        f, g = step(f, g, prm, check=check)
+    return f, g
+
+
+def fields(f, g, check: bool = True) -> Fields:
+    """Macroscopic fields of a stored lattice: Eq. 10 and the recovery."""
+    N0, T00, M = moments(f, g)
+    return recover(N0, T00, M, check=check)
+
+
+def conserved_totals(f, g):
+    """Lattice sums of N0, T00 and M (the quantities the collision conserves,
+    Sec. III.A and Eq. A8): returns a (5,) FP64 tensor."""
+    N0, T00, M = moments(f, g)
+    return torch.stack([N0.sum(), T00.sum(), M[0].sum(), M[1].sum(), M[2].sum()])
+
+
+# ----------------------------------------------------------------------------- misfit and its gradient
+def profile_misfit(f, g, P_target, u_target, w_P=1.0, w_u=1.0):
+    """L2 misfit of the pressure and velocity profiles of a stored lattice:
+    w_P sum (P - P*)^2 + w_u sum |u - u*|^2."""
+    fl = fields(f, g, check=False)
+    return w_P * ((fl.P - P_target) ** 2).sum() + w_u * ((fl.u - u_target) ** 2).sum()
+
+
+def misfit_and_gradient(e0, u0, n0, prm: Params, nsteps, P_target, u_target, w_P=1.0, w_u=1.0):
+    """Exact discrete gradient of the misfit after ``nsteps`` steps with respect to
+    (tau_v, tau_e, tau_eps) and the initial e field, by reverse-mode automatic
+    differentiation of this oracle (the library primitive torch.autograd).  The
+    initial state is g = g^eq(e0, e0/3, u0).  Returns (loss, dtau[3], de0)."""
+    tv = torch.tensor(float(prm.tau_v), dtype=DT, requires_grad=True)
+    te = torch.tensor(float(prm.tau_e), dtype=DT, requires_grad=True)
+    tp = torch.tensor(float(prm.tau_eps), dtype=DT, requires_grad=True)
+    e0 = e0.detach().clone().requires_grad_(True)
+    q = dataclasses.replace(prm, tau_v=tv, tau_e=te, tau_eps=tp,
+                            tau_q=(tv if prm.tau_q <= 0 else float(prm.tau_q)))
+    f, g = init_populations(e0, u0, n0)
+    f, g = run(f, g, q, nsteps, check=False)
+    loss = profile_misfit(f, g, P_target, u_target, w_P, w_u)
+    loss.backward()
+    return (float(loss.detach()), torch.stack([tv.grad, te.grad, tp.grad]).detach(), e0.grad.detach())
