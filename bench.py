@@ -1,0 +1,282 @@
+"""Benchmark of the fused relativistic-LB stream-collide step on GB300.
+
+Workload (default): 3-D MRT periodic box, D3Q19, 256^3 nodes, FP64, tau_v = 0.9,
+tau_e = 0.55, tau_eps = 0.8 (tau_q = tau_f = tau_v), seeded smooth random fields
+(e = e0 (1 + 0.1 modes), solenoidal u with max|u| = 0.3, n = n0 (1 + 0.05 modes)).
+A "step" is one lattice time step: one pass of the fused pull-stream + moments +
+recovery + equilibria + MRT collide over all 16.7 M nodes (one kernel launch).
+Metric: MLUPS (million lattice-node updates per second), higher is better.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload box256|box512_fp32]
+
+Prints one JSON line.  ``--impl reference`` times the CPU oracle (the plain FP64
+statement of the scheme) on the host cores over a bounded sample of the same
+workload.  Under torchrun every rank runs its own replica (the lattices are
+independent; there is no data-path collective), the elapsed time is the max over
+ranks and ``value`` counts all ranks' node updates.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import torch  # noqa: E402
+
+WORKLOADS = {
+    "box256": dict(N=256, precision="fp64", dtype="f64", bytes_per_update=608,
+                   desc="3-D MRT periodic box, D3Q19, 256^3 nodes, FP64, tau_v=0.9 tau_e=0.55 tau_eps=0.8, "
+                        "seeded smooth fields (max|u|=0.3), 500 steps"),
+    "box512_fp32": dict(N=512, precision="fp32", dtype="f32-storage/f64-recovery", bytes_per_update=304,
+                        desc="3-D MRT periodic box, D3Q19, 512^3 nodes, FP32 population storage with FP64 sums "
+                             "and recovery, same fields and taus, 200 steps"),
+}
+TAUS = dict(tau_f=0.9, tau_v=0.9, tau_e=0.55, tau_eps=0.8)
+
+# FP64 flops (FMA = 2, sqrt and division = 1) of one FP64 MRT node update,
+# counted from the per-node arithmetic of the step kernel: moments 57,
+# recovery 23, f relaxation 102 (+6 pair velocities), g relaxation 97, MRT 27.
+FLOPS_PER_UPDATE_F64 = 312
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        return dist, dist.get_rank(), ws
+    return None, 0, 1
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(seconds_budget=15.0):
+    """The oracle (plain FP64, torch CPU ops) on a bounded sample of the workload:
+    a 48^3 box of the same generator and relaxation times, as many steps as fit the
+    budget (at least 2).  Returns MLUPS and what was run."""
+    import oracle.rlb_oracle as O
+    from paper_1211_3286_gb300 import inputs as I
+    n = 48
+    e, ux, uy, uz, nn = I.periodic_box(None, shape=(n, n, n))
+    prm = O.Params(collision="mrt", **TAUS)
+    f, g = O.init_populations(e, torch.stack([ux, uy, uz]), nn)
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < 2 or (time.perf_counter() - t0 < seconds_budget and steps < 200):
+        f, g = O.step(f, g, prm)
+        steps += 1
+    dt = time.perf_counter() - t0
+    return {"value": n ** 3 * steps / dt / 1e6, "unit": "MLUPS", "cores": torch.get_num_threads(),
+            "kind": "oracle", "sample": "%d^3 MRT box, %d steps, same generator and taus, FP64 oracle" % (n, steps),
+            "seconds": round(dt, 2)}
+
+
+def run_reference(args):
+    dist, rank, ws = _dist()
+    if rank != 0:
+        return
+    wl = WORKLOADS[args.workload]
+    budget = max(10.0, 2.0 * args.steps)
+    cb = cpu_baseline(min(budget, 60.0))
+    line = {"impl": "reference", "metric": "MLUPS", "value": cb["value"], "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["desc"], "reference_sample": cb["sample"]},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    dist, rank, ws = _dist()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (librlb has no CPU path)")
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1211_3286_gb300 import inputs as I
+    from paper_1211_3286_gb300.lattice import Lattice
+
+    wl = WORKLOADS[args.workload]
+    N = wl["N"]
+    nodes = N ** 3
+    stream = torch.cuda.Stream()
+    e, ux, uy, uz, n = I.periodic_box(N, device="cuda")
+    with torch.cuda.stream(stream):
+        lat = Lattice((N, N, N), collision="mrt", precision=wl["precision"], stream=stream, **TAUS)
+    lat.set_fields(e, ux, uy, uz, n)
+    del e, ux, uy, uz, n
+    torch.cuda.synchronize()
+
+    # warm-up
+    lat.step(args.warmup)
+    lat.check()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as cs:
+        ev0.record(stream)
+        lat.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    lat.check()
+    ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    clocks = cs.summary()
+    per_launch_s = ms / 1e3 / args.steps
+    mlups = nodes * args.steps * ws / (ms / 1e3) / 1e6
+
+    # end to end through the C ABI with pinned host buffers: upload the initial
+    # fields, run the steps, read the final fields back
+    e2e = None
+    if not args.no_e2e:
+        hf = [t.cpu().pin_memory() for t in I.periodic_box(N, device="cuda")]
+        outs = [torch.empty((N, N, N), dtype=torch.float64).pin_memory() for _ in range(6)]
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        t0 = time.perf_counter()
+        lat.set_fields(*hf)
+        lat.step(args.steps)
+        from paper_1211_3286_gb300 import _lib as L
+        import ctypes
+        L.rlb_get_fields(lat.handle, *[ctypes.c_void_p(o.data_ptr()) for o in outs], L.RLB_HOST)
+        dt = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([dt], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": nodes * args.steps * ws / dt / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": 5 * nodes * 8 / args.steps, "d2h_bytes_per_step": 6 * nodes * 8 / args.steps,
+               "what": "rlb_set_fields(host) + rlb_step(K) + rlb_get_fields(host), pinned buffers"}
+    lat.close()
+
+    hbm_peak, peak_kind = _peaks()
+    gbs = wl["bytes_per_update"] * nodes / per_launch_s / 1e9
+    hbm = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+           "traffic": None, "peak_kind": peak_kind}
+    roof = hbm
+    if wl["precision"] == "fp64":
+        # FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz (unit counts and max clock)
+        fp64_peak = 152 * 2 * 2 * 2.07
+        gfl = FLOPS_PER_UPDATE_F64 * nodes / per_launch_s / 1e9
+        alu = {"bound": "alu", "achieved": gfl, "peak": fp64_peak, "unit": "GFLOP/s", "frac": gfl / fp64_peak,
+               "traffic": None, "peak_kind": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
+               "hbm_frac": gbs / hbm_peak}
+        if alu["frac"] > hbm["frac"]:
+            roof = alu
+    if rank == 0:
+        line = {"metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": wl["dtype"], "data": "synthetic",
+                "config": {"workload": wl["desc"], "nodes": nodes, "l2": "lattice (%.1f GB) larger than L2"
+                           % (2 * 38 * nodes * (8 if wl["precision"] == "fp64" else 4) / 1e9),
+                           "parallelism": "replicas" if ws > 1 else "single"},
+                "roofline": roof, "hbm_roofline": hbm, "clocks": clocks, "e2e": e2e,
+                "gpu_launches": args.steps}
+        if not args.no_cpu_baseline and ws == 1:
+            line["cpu_baseline"] = cpu_baseline(15.0)
+        print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="box256", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

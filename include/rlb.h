@@ -1,0 +1,147 @@
+/*
+ * rlb.h -- C ABI of librlb, a GB300 (sm_103a) implementation of the relativistic
+ * lattice Boltzmann (RLB) scheme analysed by Li, Luo & Li, "Lattice Boltzmann
+ * method for relativistic hydrodynamics: issues on conservation law of particle
+ * number and discontinuities" (arXiv 1211.3286).
+ *
+ * The library advances two D3Q19 distribution sets on one GPU:
+ *   f_a  (particle number N^mu, BGK relaxation, Eq. 5, equilibrium Eq. 7),
+ *   g_a  (energy-momentum T^{mu nu}, BGK Eq. 6 or MRT Eqs. 30-35, equilibria Eqs. 8-9),
+ * with the macroscopic fields recovered per node from Eq. 10 under the
+ * ultrarelativistic equation of state P = e/3 (closed form, no iteration):
+ *   sigma = (2 T00 + sqrt(4 T00^2 - 3 |M|^2)) / 3,  u = M / sigma,  P = sigma - T00,
+ *   e = 3 P,  gamma = 1 / sqrt(1 - u^2),  n = N0 / gamma,
+ * where N0 = sum f, T00 = sum g, M = sum e_a g_a.
+ *
+ * Conventions shared by every call
+ *   - All entry points are extern "C", return an int status (RLB_OK = 0 on
+ *     success) unless stated, and never throw.  On failure the handle's
+ *     rlb_last_error() string says why.
+ *   - Lattices are x-fastest: field arrays hold nx*ny*nz values indexed
+ *     (z*ny + y)*nx + x.  The quasi-1D tube is {nx = L, ny = 1, nz = 1}.
+ *   - Pointers tagged RLB_HOST are ordinary host memory; RLB_DEVICE pointers are
+ *     device memory of the handle's GPU (for example a torch tensor's data_ptr()).
+ *     The library never keeps a caller's pointer past the call.
+ *   - Calls that launch work are asynchronous on the configured stream unless
+ *     they say they synchronise.  Device-side detection of a non-physical state
+ *     (4 T00^2 - 3|M|^2 < 0, T00 <= 0, e <= 0, |u| >= 1 or NaN) is reported by
+ *     the next synchronising call as RLB_ENONPHYS, with the first bad node index
+ *     in rlb_last_error().
+ *   - The library owns the device lattices it allocates in rlb_create and frees
+ *     them in rlb_destroy.
+ */
+#ifndef RLB_H
+#define RLB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define RLB_OK        0
+#define RLB_EINVAL    1  /* invalid argument or non-physical input field */
+#define RLB_ENOMEM    2  /* device or host allocation failed */
+#define RLB_ECUDA     3  /* a CUDA runtime call failed */
+#define RLB_ENONPHYS  4  /* the device flagged a non-physical node during stepping */
+#define RLB_ETIMEOUT  5  /* a bounded device-side wait gave up */
+
+/* lattice, equation of state, collision, boundary, precision, memory space */
+#define RLB_D3Q19               19
+#define RLB_EOS_ULTRAREL         1   /* P = e / 3 */
+#define RLB_BGK                  0   /* Eq. 6 for g */
+#define RLB_MRT                  1   /* Eqs. 30-35 (D3Q19 moment basis) for g */
+#define RLB_PERIODIC             0
+#define RLB_ZERO_GRADIENT        1   /* "open" end: a pull from outside takes the edge node */
+#define RLB_FP64                 0   /* populations stored and updated in FP64 */
+#define RLB_FP32_STORAGE         1   /* populations stored in FP32; sums, recovery, gamma in FP64 */
+#define RLB_HOST                 0
+#define RLB_DEVICE               1
+
+/*
+ * Problem statement of one lattice: the lattice with c = dx/dt = 1 (Sec. III.B),
+ * the EOS, the relaxation times tau_f (Eq. 5), tau_v / tau_e / tau_eps / tau_q
+ * (the MRT rates of Eq. 31 and Sec. V.B), the boundary type per axis and the
+ * storage precision.
+ *   tau_f    relaxation time of f (BGK).  Must be > 0.5.
+ *   tau_v    shear time; also the single g time under RLB_BGK.  > 0.5.
+ *   tau_e    bulk (energy moment) time, MRT only.  > 0.5.
+ *   tau_eps  energy-square moment time, MRT only.  > 0.5.
+ *   tau_q    energy-flux moment time, MRT only; <= 0 means tau_q = tau_v.
+ *   stream   a cudaStream_t (NULL = legacy default stream) on which all work of
+ *            this handle is enqueued.
+ */
+typedef struct rlb_config {
+  int nx, ny, nz;
+  int lattice;      /* RLB_D3Q19 */
+  int eos;          /* RLB_EOS_ULTRAREL */
+  int collision;    /* RLB_BGK | RLB_MRT */
+  double tau_f, tau_v, tau_e, tau_eps, tau_q;
+  int bc[3];        /* per axis x, y, z: RLB_PERIODIC | RLB_ZERO_GRADIENT */
+  int precision;    /* RLB_FP64 | RLB_FP32_STORAGE */
+  void* stream;
+} rlb_config;
+
+typedef struct rlb_handle rlb_handle;
+
+/* Allocate a lattice on the current CUDA device.  Returns RLB_EINVAL for a
+ * zero or negative extent, an unknown enum, or any tau <= 0.5; RLB_ENOMEM if the
+ * two lattices (2 x 38 x nodes x 8 or 4 bytes) do not fit.  *out is set only on
+ * success. */
+int rlb_create(const rlb_config* cfg, rlb_handle** out);
+
+/* Free the handle and its device memory (synchronises its stream).  NULL is a no-op. */
+void rlb_destroy(rlb_handle* h);
+
+/* Message describing the last failure on h (or on a failed rlb_create when h is
+ * NULL); never NULL. */
+const char* rlb_last_error(const rlb_handle* h);
+
+/* Set the state to equilibrium of the given fields: f = f^eq(n, u) (Eq. 7),
+ * g = g^eq(e, P = e/3, u) (Eqs. 8-9).  e, ux, uy, uz, n each hold nx*ny*nz FP64
+ * values in `where` memory; e > 0, n > 0 and |u| < 1 are required (RLB_EINVAL
+ * otherwise, state unchanged).  Synchronises. */
+int rlb_set_fields(rlb_handle* h, const double* e, const double* ux, const double* uy,
+                   const double* uz, const double* n, int where);
+
+/* Advance nsteps time steps (nsteps >= 0): each step pulls f and g from x - e_a
+ * (periodic axes wrap, zero-gradient axes clamp), recovers the fields from
+ * Eq. 10, and relaxes f by Eq. 5 and g by Eq. 6 (BGK) or Eq. 35 (MRT).
+ * Asynchronous on the handle's stream. */
+int rlb_step(rlb_handle* h, int nsteps);
+
+/* Wait for the handle's stream and report a device-flagged non-physical node
+ * (RLB_ENONPHYS) since the last check; clears the flag. */
+int rlb_check(rlb_handle* h);
+
+/* Macroscopic fields of the current state (Eq. 10 plus the recovery): e, P,
+ * ux, uy, uz, n, each nx*ny*nz FP64 values in `where` memory.  Any pointer may be
+ * NULL to skip that field.  Synchronises and reports RLB_ENONPHYS like rlb_check. */
+int rlb_get_fields(rlb_handle* h, double* e, double* P, double* ux, double* uy, double* uz,
+                   double* n, int where);
+
+/* Lattice sums of the conserved densities of the current state, in FP64 with a
+ * fixed (deterministic) reduction order: out[0] = sum N0, out[1] = sum T00,
+ * out[2..4] = sum M_x, M_y, M_z (the quantities Eq. A8 leaves unchanged under
+ * collision).  out is host memory.  Synchronises. */
+int rlb_conserved_totals(rlb_handle* h, double out[5]);
+
+/* Number of bytes of one raw state: 2 x 19 x nodes x (8 for RLB_FP64, 4 for
+ * RLB_FP32_STORAGE).  Layout: f[19][nz][ny][nx] followed by g[19][nz][ny][nx],
+ * post-collision populations of the current time step. */
+size_t rlb_state_bytes(const rlb_handle* h);
+
+/* Copy the raw state out to / in from `where` memory of rlb_state_bytes(h)
+ * bytes (checkpoint and resume).  Synchronise. */
+int rlb_save_state(rlb_handle* h, void* buf, int where);
+int rlb_load_state(rlb_handle* h, const void* buf, int where);
+
+/* Number of time steps taken since the last rlb_set_fields / rlb_load_state. */
+long long rlb_steps_done(const rlb_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RLB_H */

@@ -1,0 +1,10 @@
+// rlb_internal.h -- helpers shared by the translation units of librlb (not part of the ABI).
+#pragma once
+#include <string>
+
+namespace rlb {
+// Checks the relaxation times of a problem statement (every tau > 0.5, tau_q <= 0
+// meaning tau_v); returns RLB_OK or RLB_EINVAL with the reason in `why`.
+int validate_taus(double tau_f, double tau_v, double tau_e, double tau_eps, double tau_q, int collision,
+                  std::string& why);
+}  // namespace rlb

@@ -1,0 +1,489 @@
+// rlb_lattice.cu -- the lattice handle of librlb: allocation, initial state,
+// fused pull-stream + collide step kernels, field output, conserved totals and
+// raw state I/O (the C ABI declared in include/rlb.h).
+//
+// Data layout in HBM: two lattices (read / write, swapped every step), each
+// holding f[19][nz][ny][nx] followed by g[19][nz][ny][nx] in the storage
+// precision (FP64, or FP32 for RLB_FP32_STORAGE).  One thread owns one node:
+// it pulls the 38 populations from x - e_a (x-adjacent threads read adjacent
+// addresses, so every load is coalesced), runs the per-node collide of
+// rlb_node.cuh in registers, and writes the 38 results to its own node.
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/rlb.h"
+#include "rlb_internal.h"
+#include "rlb_node.cuh"
+
+using namespace rlb;
+
+struct rlb_handle {
+  rlb_config cfg;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  size_t nodes = 0;
+  size_t esize = 8;
+  void* lat[2] = {nullptr, nullptr};
+  int cur = 0;
+  unsigned long long* d_bad = nullptr;   // smallest non-physical node index, ULLONG_MAX if none
+  double* d_part = nullptr;              // reduction partials
+  double* d_stage = nullptr;             // 6 x nodes FP64 staging for host field I/O
+  StepConst k{};
+  long long steps = 0;
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+int fail(rlb_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_create_error = msg;
+  return code;
+}
+
+int cuda_fail(rlb_handle* h, cudaError_t e, const char* what) {
+  return fail(h, RLB_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define RLB_CUDA(h, call)                               \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+  } while (0)
+
+constexpr int kBlockX = 128;
+constexpr int kRedBlocks = 608;   // 4 x 152 SMs; fixed so the reduction order is fixed
+constexpr int kRedThreads = 256;
+
+struct Geo {
+  int nx, ny, nz;
+  int bcx, bcy, bcz;   // 1 = zero-gradient
+  unsigned long long plane;   // nodes
+};
+
+__device__ __forceinline__ int src_minus(int i, int n, int zg) {  // source of a pull with c = +1
+  return i > 0 ? i - 1 : (zg ? 0 : n - 1);
+}
+__device__ __forceinline__ int src_plus(int i, int n, int zg) {   // source of a pull with c = -1
+  return i < n - 1 ? i + 1 : (zg ? n - 1 : 0);
+}
+
+template <typename S>
+__device__ __forceinline__ S ldg_nc(const S* p) { return __ldg(p); }
+
+// Gather the 19 populations of one distribution arriving at node (x, y, z):
+// link a comes from (x - cx, y - cy, z - cz).
+template <typename S>
+__device__ __forceinline__ void pull19(const S* __restrict__ base, unsigned long long plane, const int (&xs)[3],
+                                       const unsigned (&row)[3][3], S (&v)[19]) {
+#pragma unroll
+  for (int a = 0; a < 19; ++a) {
+    const int cx = link_cx(a), cy = link_cy(a), cz = link_cz(a);
+    const unsigned idx = row[1 - cz][1 - cy] + (unsigned)xs[1 - cx];
+    v[a] = ldg_nc(base + (unsigned long long)a * plane + idx);
+  }
+}
+
+template <typename S, bool MRT, bool QSEP>
+__global__ void __launch_bounds__(kBlockX) k_step(const S* __restrict__ src, S* __restrict__ dst, Geo geo,
+                                                  StepConst k, unsigned long long* __restrict__ bad) {
+  const int x = blockIdx.x * kBlockX + threadIdx.x;
+  if (x >= geo.nx) return;
+  const int y = blockIdx.y, z = blockIdx.z;
+  // source coordinates for offsets c = +1, 0, -1 (index 0, 1, 2 = 1 - c)
+  const int xs[3] = {src_minus(x, geo.nx, geo.bcx), x, src_plus(x, geo.nx, geo.bcx)};
+  const int ys[3] = {src_minus(y, geo.ny, geo.bcy), y, src_plus(y, geo.ny, geo.bcy)};
+  const int zs[3] = {src_minus(z, geo.nz, geo.bcz), z, src_plus(z, geo.nz, geo.bcz)};
+  unsigned row[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) row[i][j] = ((unsigned)zs[i] * (unsigned)geo.ny + (unsigned)ys[j]) * (unsigned)geo.nx;
+
+  S f[19], g[19];
+  pull19<S>(src, geo.plane, xs, row, f);
+  pull19<S>(src + 19ull * geo.plane, geo.plane, xs, row, g);
+  bool b;
+  if constexpr (sizeof(S) == 8) b = node_collide_f64<MRT, QSEP>(f, g, k);
+  else b = node_collide_f32s<MRT, QSEP>(f, g, k);
+  const unsigned node = row[1][1] + (unsigned)x;
+  if (b) atomicMin(bad, (unsigned long long)node);
+#pragma unroll
+  for (int a = 0; a < 19; ++a) {
+    dst[(unsigned long long)a * geo.plane + node] = f[a];
+    dst[(19ull + a) * geo.plane + node] = g[a];
+  }
+}
+
+// f = f^eq, g = g^eq of the given FP64 fields; flags invalid input nodes.
+template <typename S>
+__global__ void k_init(S* __restrict__ lat, unsigned long long nodes, const double* __restrict__ e,
+                       const double* __restrict__ ux, const double* __restrict__ uy, const double* __restrict__ uz,
+                       const double* __restrict__ n, unsigned long long* __restrict__ bad) {
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < nodes;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const double ei = e[i], xi = ux[i], yi = uy[i], zi = uz[i], ni = n[i];
+    const double u2 = xi * xi + yi * yi + zi * zi;
+    if (!(ei > 0.0) || !(ni > 0.0) || !(u2 < 1.0) || !isfinite(ei) || !isfinite(ni)) {
+      atomicMin(bad, i);
+      continue;
+    }
+    double f[19], g[19];
+    node_equilibrium(ei, xi, yi, zi, ni, f, g);
+#pragma unroll
+    for (int a = 0; a < 19; ++a) {
+      lat[(unsigned long long)a * nodes + i] = (S)f[a];
+      lat[(19ull + a) * nodes + i] = (S)g[a];
+    }
+  }
+}
+
+// Moments of the stored populations of node i (Eq. 10), FP64.
+template <typename S>
+__device__ __forceinline__ void stored_moments(const S* __restrict__ lat, unsigned long long nodes,
+                                               unsigned long long i, NodeMacro& m) {
+  S f[19], g[19];
+#pragma unroll
+  for (int a = 0; a < 19; ++a) {
+    f[a] = lat[(unsigned long long)a * nodes + i];
+    g[a] = lat[(19ull + a) * nodes + i];
+  }
+  double sp[9], dp[9], Sa, Sd;
+  node_moments<S>(f, g, sp, dp, Sa, Sd, m);
+}
+
+template <typename S>
+__global__ void k_fields(const S* __restrict__ lat, unsigned long long nodes, double* __restrict__ e,
+                         double* __restrict__ P, double* __restrict__ ux, double* __restrict__ uy,
+                         double* __restrict__ uz, double* __restrict__ n, unsigned long long* __restrict__ bad) {
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < nodes;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    NodeMacro m;
+    stored_moments<S>(lat, nodes, i, m);
+    node_recover(m);
+    if (m.bad) atomicMin(bad, i);
+    e[i] = 3.0 * m.P;
+    P[i] = m.P;
+    ux[i] = m.ux;
+    uy[i] = m.uy;
+    uz[i] = m.uz;
+    n[i] = m.N0 * sqrt(1.0 - m.u2);
+  }
+}
+
+// Deterministic two-pass sum of (N0, T00, Mx, My, Mz) over all nodes.
+template <typename S>
+__global__ void __launch_bounds__(kRedThreads) k_totals_part(const S* __restrict__ lat, unsigned long long nodes,
+                                                             double* __restrict__ part) {
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (unsigned long long i = blockIdx.x * (unsigned long long)kRedThreads + threadIdx.x; i < nodes;
+       i += (unsigned long long)kRedBlocks * kRedThreads) {
+    NodeMacro m;
+    stored_moments<S>(lat, nodes, i, m);
+    acc[0] += m.N0; acc[1] += m.T00; acc[2] += m.Mx; acc[3] += m.My; acc[4] += m.Mz;
+  }
+  __shared__ double sh[5][kRedThreads];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) sh[c][threadIdx.x] = acc[c];
+  __syncthreads();
+  for (int s = kRedThreads / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s)
+#pragma unroll
+      for (int c = 0; c < 5; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x < 5) part[blockIdx.x * 5 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_totals_final(const double* __restrict__ part, double* __restrict__ out) {
+  __shared__ double sh[5][kRedThreads];
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (int b = threadIdx.x; b < kRedBlocks; b += kRedThreads)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) acc[c] += part[b * 5 + c];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) sh[c][threadIdx.x] = acc[c];
+  __syncthreads();
+  for (int s = kRedThreads / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s)
+#pragma unroll
+      for (int c = 0; c < 5; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x < 5) out[threadIdx.x] = sh[threadIdx.x][0];
+}
+
+Geo make_geo(const rlb_handle* h) {
+  Geo g;
+  g.nx = h->cfg.nx; g.ny = h->cfg.ny; g.nz = h->cfg.nz;
+  g.bcx = h->cfg.bc[0] == RLB_ZERO_GRADIENT;
+  g.bcy = h->cfg.bc[1] == RLB_ZERO_GRADIENT;
+  g.bcz = h->cfg.bc[2] == RLB_ZERO_GRADIENT;
+  g.plane = h->nodes;
+  return g;
+}
+
+bool qsep(const rlb_config& c) { return c.collision == RLB_MRT && c.tau_q > 0 && c.tau_q != c.tau_v; }
+
+template <typename S>
+cudaError_t launch_step(rlb_handle* h, const void* src, void* dst) {
+  const Geo geo = make_geo(h);
+  dim3 grid((geo.nx + kBlockX - 1) / kBlockX, geo.ny, geo.nz);
+  const bool mrt = h->cfg.collision == RLB_MRT, q = qsep(h->cfg);
+  const S* s = (const S*)src;
+  S* d = (S*)dst;
+  if (!mrt) k_step<S, false, false><<<grid, kBlockX, 0, h->stream>>>(s, d, geo, h->k, h->d_bad);
+  else if (!q) k_step<S, true, false><<<grid, kBlockX, 0, h->stream>>>(s, d, geo, h->k, h->d_bad);
+  else k_step<S, true, true><<<grid, kBlockX, 0, h->stream>>>(s, d, geo, h->k, h->d_bad);
+  return cudaGetLastError();
+}
+
+int check_flag(rlb_handle* h) {
+  RLB_CUDA(h, cudaStreamSynchronize(h->stream));
+  unsigned long long bad = ULLONG_MAX;
+  RLB_CUDA(h, cudaMemcpy(&bad, h->d_bad, sizeof(bad), cudaMemcpyDeviceToHost));
+  if (bad != ULLONG_MAX) {
+    const unsigned long long reset = ULLONG_MAX;
+    RLB_CUDA(h, cudaMemcpy(h->d_bad, &reset, sizeof(reset), cudaMemcpyHostToDevice));
+    char buf[160];
+    std::snprintf(buf, sizeof buf, "non-physical state at node %llu (x=%llu, y=%llu, z=%llu)", bad,
+                  bad % (unsigned long long)h->cfg.nx, (bad / h->cfg.nx) % (unsigned long long)h->cfg.ny,
+                  bad / ((unsigned long long)h->cfg.nx * h->cfg.ny));
+    return fail(h, RLB_ENONPHYS, buf);
+  }
+  return RLB_OK;
+}
+
+int ensure_stage(rlb_handle* h) {
+  if (h->d_stage) return RLB_OK;
+  cudaError_t e = cudaMalloc(&h->d_stage, 6 * h->nodes * sizeof(double));
+  if (e != cudaSuccess) {
+    h->d_stage = nullptr;
+    return fail(h, RLB_ENOMEM, "cannot allocate field staging buffer");
+  }
+  return RLB_OK;
+}
+
+int grid_for(size_t nodes) {
+  size_t b = (nodes + 255) / 256;
+  return (int)(b < 152 * 32 ? (b ? b : 1) : 152 * 32);
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------------- internal helpers
+namespace rlb {
+int validate_taus(double tau_f, double tau_v, double tau_e, double tau_eps, double tau_q, int collision,
+                  std::string& why) {
+  if (!(tau_f > 0.5) || !(tau_v > 0.5)) { why = "tau_f and tau_v must be > 0.5"; return RLB_EINVAL; }
+  if (collision == RLB_MRT) {
+    if (!(tau_e > 0.5) || !(tau_eps > 0.5)) { why = "tau_e and tau_eps must be > 0.5"; return RLB_EINVAL; }
+    if (tau_q > 0 && !(tau_q > 0.5)) { why = "tau_q must be > 0.5 (or <= 0 for tau_v)"; return RLB_EINVAL; }
+  }
+  return RLB_OK;
+}
+}  // namespace rlb
+
+// ----------------------------------------------------------------------------- C ABI
+extern "C" int rlb_create(const rlb_config* cfg, rlb_handle** out) {
+  if (!cfg || !out) return fail(nullptr, RLB_EINVAL, "null argument");
+  if (cfg->nx <= 0 || cfg->ny <= 0 || cfg->nz <= 0) return fail(nullptr, RLB_EINVAL, "lattice extents must be > 0");
+  if (cfg->lattice != RLB_D3Q19) return fail(nullptr, RLB_EINVAL, "only RLB_D3Q19 is supported");
+  if (cfg->eos != RLB_EOS_ULTRAREL) return fail(nullptr, RLB_EINVAL, "only RLB_EOS_ULTRAREL (P = e/3) is supported");
+  if (cfg->collision != RLB_BGK && cfg->collision != RLB_MRT) return fail(nullptr, RLB_EINVAL, "unknown collision");
+  if (cfg->precision != RLB_FP64 && cfg->precision != RLB_FP32_STORAGE)
+    return fail(nullptr, RLB_EINVAL, "unknown precision");
+  for (int a = 0; a < 3; ++a)
+    if (cfg->bc[a] != RLB_PERIODIC && cfg->bc[a] != RLB_ZERO_GRADIENT)
+      return fail(nullptr, RLB_EINVAL, "unknown boundary type");
+  std::string why;
+  if (rlb::validate_taus(cfg->tau_f, cfg->tau_v, cfg->tau_e, cfg->tau_eps, cfg->tau_q, cfg->collision, why))
+    return fail(nullptr, RLB_EINVAL, why);
+  const unsigned long long nodes = (unsigned long long)cfg->nx * cfg->ny * cfg->nz;
+  if (nodes >= (1ull << 32) || (unsigned long long)cfg->ny * cfg->nz > 65535ull * 65535ull || cfg->ny > 65535 ||
+      cfg->nz > 65535)
+    return fail(nullptr, RLB_EINVAL, "lattice too large (nodes must be < 2^32, ny and nz <= 65535)");
+
+  rlb_handle* h = new rlb_handle();
+  h->cfg = *cfg;
+  h->stream = (cudaStream_t)cfg->stream;
+  h->nodes = nodes;
+  h->esize = cfg->precision == RLB_FP64 ? 8 : 4;
+  h->k = make_step_const(cfg->tau_f, cfg->tau_v, cfg->tau_e, cfg->tau_eps, cfg->tau_q, cfg->collision == RLB_MRT);
+  cudaGetDevice(&h->device);
+  const size_t bytes = 38 * h->nodes * h->esize;
+  for (int i = 0; i < 2; ++i) {
+    if (cudaMalloc(&h->lat[i], bytes) != cudaSuccess) {
+      cudaGetLastError();
+      rlb_destroy(h);
+      return fail(nullptr, RLB_ENOMEM, "cannot allocate the two lattices");
+    }
+  }
+  if (cudaMalloc(&h->d_bad, sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMalloc(&h->d_part, (kRedBlocks * 5 + 8) * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    rlb_destroy(h);
+    return fail(nullptr, RLB_ENOMEM, "cannot allocate small device buffers");
+  }
+  const unsigned long long none = ULLONG_MAX;
+  if (cudaMemcpy(h->d_bad, &none, sizeof none, cudaMemcpyHostToDevice) != cudaSuccess) {
+    rlb_destroy(h);
+    return fail(nullptr, RLB_ECUDA, "cannot initialise device flag");
+  }
+  *out = h;
+  return RLB_OK;
+}
+
+extern "C" void rlb_destroy(rlb_handle* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  for (int i = 0; i < 2; ++i)
+    if (h->lat[i]) cudaFree(h->lat[i]);
+  if (h->d_bad) cudaFree(h->d_bad);
+  if (h->d_part) cudaFree(h->d_part);
+  if (h->d_stage) cudaFree(h->d_stage);
+  delete h;
+}
+
+extern "C" const char* rlb_last_error(const rlb_handle* h) {
+  return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+extern "C" int rlb_set_fields(rlb_handle* h, const double* e, const double* ux, const double* uy, const double* uz,
+                              const double* n, int where) {
+  if (!h || !e || !ux || !uy || !uz || !n) return fail(h, RLB_EINVAL, "null argument");
+  if (where != RLB_HOST && where != RLB_DEVICE) return fail(h, RLB_EINVAL, "where must be RLB_HOST or RLB_DEVICE");
+  const size_t N = h->nodes;
+  const double *de = e, *dx = ux, *dy = uy, *dz = uz, *dn = n;
+  if (where == RLB_HOST) {
+    for (size_t i = 0; i < N; ++i) {
+      const double u2 = ux[i] * ux[i] + uy[i] * uy[i] + uz[i] * uz[i];
+      if (!(e[i] > 0) || !(n[i] > 0) || !(u2 < 1.0) || !std::isfinite(e[i]) || !std::isfinite(n[i])) {
+        char buf[128];
+        std::snprintf(buf, sizeof buf, "invalid field at node %zu (need e > 0, n > 0, |u| < 1)", i);
+        return fail(h, RLB_EINVAL, buf);
+      }
+    }
+    int rc = ensure_stage(h);
+    if (rc) return rc;
+    double* s = h->d_stage;
+    const double* src[5] = {e, ux, uy, uz, n};
+    for (int c = 0; c < 5; ++c)
+      RLB_CUDA(h, cudaMemcpyAsync(s + c * N, src[c], N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    de = s; dx = s + N; dy = s + 2 * N; dz = s + 3 * N; dn = s + 4 * N;
+  }
+  // validate on device (RLB_DEVICE inputs) and build the equilibrium state in the spare lattice
+  const int spare = 1 - h->cur;
+  const unsigned long long none = ULLONG_MAX;
+  RLB_CUDA(h, cudaMemcpyAsync(h->d_bad, &none, sizeof none, cudaMemcpyHostToDevice, h->stream));
+  if (h->esize == 8)
+    k_init<double><<<grid_for(N), 256, 0, h->stream>>>((double*)h->lat[spare], N, de, dx, dy, dz, dn, h->d_bad);
+  else
+    k_init<float><<<grid_for(N), 256, 0, h->stream>>>((float*)h->lat[spare], N, de, dx, dy, dz, dn, h->d_bad);
+  RLB_CUDA(h, cudaGetLastError());
+  RLB_CUDA(h, cudaStreamSynchronize(h->stream));
+  unsigned long long bad = ULLONG_MAX;
+  RLB_CUDA(h, cudaMemcpy(&bad, h->d_bad, sizeof bad, cudaMemcpyDeviceToHost));
+  if (bad != ULLONG_MAX) {
+    RLB_CUDA(h, cudaMemcpy(h->d_bad, &none, sizeof none, cudaMemcpyHostToDevice));
+    char buf[128];
+    std::snprintf(buf, sizeof buf, "invalid field at node %llu (need e > 0, n > 0, |u| < 1)", bad);
+    return fail(h, RLB_EINVAL, buf);
+  }
+  h->cur = spare;
+  h->steps = 0;
+  return RLB_OK;
+}
+
+extern "C" int rlb_step(rlb_handle* h, int nsteps) {
+  if (!h) return fail(h, RLB_EINVAL, "null handle");
+  if (nsteps < 0) return fail(h, RLB_EINVAL, "nsteps must be >= 0");
+  for (int s = 0; s < nsteps; ++s) {
+    const void* src = h->lat[h->cur];
+    void* dst = h->lat[1 - h->cur];
+    cudaError_t e = h->esize == 8 ? launch_step<double>(h, src, dst) : launch_step<float>(h, src, dst);
+    if (e != cudaSuccess) return cuda_fail(h, e, "step kernel launch");
+    h->cur = 1 - h->cur;
+    ++h->steps;
+  }
+  return RLB_OK;
+}
+
+extern "C" int rlb_check(rlb_handle* h) {
+  if (!h) return fail(h, RLB_EINVAL, "null handle");
+  return check_flag(h);
+}
+
+extern "C" int rlb_get_fields(rlb_handle* h, double* e, double* P, double* ux, double* uy, double* uz, double* n,
+                              int where) {
+  if (!h) return fail(h, RLB_EINVAL, "null handle");
+  if (where != RLB_HOST && where != RLB_DEVICE) return fail(h, RLB_EINVAL, "where must be RLB_HOST or RLB_DEVICE");
+  int rc = ensure_stage(h);
+  if (rc) return rc;
+  const size_t N = h->nodes;
+  double* s = h->d_stage;
+  double* dev[6] = {s, s + N, s + 2 * N, s + 3 * N, s + 4 * N, s + 5 * N};
+  double* want[6] = {e, P, ux, uy, uz, n};
+  if (where == RLB_DEVICE)
+    for (int c = 0; c < 6; ++c)
+      if (want[c]) dev[c] = want[c];
+  if (h->esize == 8)
+    k_fields<double><<<grid_for(N), 256, 0, h->stream>>>((const double*)h->lat[h->cur], N, dev[0], dev[1], dev[2],
+                                                          dev[3], dev[4], dev[5], h->d_bad);
+  else
+    k_fields<float><<<grid_for(N), 256, 0, h->stream>>>((const float*)h->lat[h->cur], N, dev[0], dev[1], dev[2],
+                                                         dev[3], dev[4], dev[5], h->d_bad);
+  RLB_CUDA(h, cudaGetLastError());
+  if (where == RLB_HOST)
+    for (int c = 0; c < 6; ++c)
+      if (want[c])
+        RLB_CUDA(h, cudaMemcpyAsync(want[c], dev[c], N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  return check_flag(h);
+}
+
+extern "C" int rlb_conserved_totals(rlb_handle* h, double out[5]) {
+  if (!h || !out) return fail(h, RLB_EINVAL, "null argument");
+  const size_t N = h->nodes;
+  if (h->esize == 8)
+    k_totals_part<double><<<kRedBlocks, kRedThreads, 0, h->stream>>>((const double*)h->lat[h->cur], N, h->d_part);
+  else
+    k_totals_part<float><<<kRedBlocks, kRedThreads, 0, h->stream>>>((const float*)h->lat[h->cur], N, h->d_part);
+  RLB_CUDA(h, cudaGetLastError());
+  k_totals_final<<<1, kRedThreads, 0, h->stream>>>(h->d_part, h->d_part + kRedBlocks * 5);
+  RLB_CUDA(h, cudaGetLastError());
+  RLB_CUDA(h, cudaMemcpyAsync(out, h->d_part + kRedBlocks * 5, 5 * sizeof(double), cudaMemcpyDeviceToHost,
+                              h->stream));
+  RLB_CUDA(h, cudaStreamSynchronize(h->stream));
+  return RLB_OK;
+}
+
+extern "C" size_t rlb_state_bytes(const rlb_handle* h) { return h ? 38 * h->nodes * h->esize : 0; }
+
+extern "C" int rlb_save_state(rlb_handle* h, void* buf, int where) {
+  if (!h || !buf) return fail(h, RLB_EINVAL, "null argument");
+  if (where != RLB_HOST && where != RLB_DEVICE) return fail(h, RLB_EINVAL, "where must be RLB_HOST or RLB_DEVICE");
+  RLB_CUDA(h, cudaMemcpyAsync(buf, h->lat[h->cur], rlb_state_bytes(h),
+                              where == RLB_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, h->stream));
+  RLB_CUDA(h, cudaStreamSynchronize(h->stream));
+  return RLB_OK;
+}
+
+extern "C" int rlb_load_state(rlb_handle* h, const void* buf, int where) {
+  if (!h || !buf) return fail(h, RLB_EINVAL, "null argument");
+  if (where != RLB_HOST && where != RLB_DEVICE) return fail(h, RLB_EINVAL, "where must be RLB_HOST or RLB_DEVICE");
+  RLB_CUDA(h, cudaMemcpyAsync(h->lat[h->cur], buf, rlb_state_bytes(h),
+                              where == RLB_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->stream));
+  RLB_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->steps = 0;
+  return RLB_OK;
+}
+
+extern "C" long long rlb_steps_done(const rlb_handle* h) { return h ? h->steps : -1; }

@@ -1,0 +1,261 @@
+"""GPU parity of the librlb lattice step against the CPU oracle (through the C ABI).
+
+Bar: FP64 fields within 1e-12 normwise relative error of the oracle; FP32
+population storage within the bound derived from its rounding (see
+test_fp32_storage_error_bound).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle.rlb_oracle as O
+from paper_1211_3286_gb300 import inputs as I
+from tests.helpers import FIELDS, field_errors, oracle_bc, oracle_fields
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1211_3286_gb300 import build
+    build.build()
+
+
+def _lattice(shape, **kw):
+    from paper_1211_3286_gb300.lattice import Lattice
+    return Lattice(shape, **kw)
+
+
+def _run_both(e, ux, uy, uz, n, steps, collision, taus, bc, precision="fp64"):
+    tau_f, tau_v, tau_e, tau_eps, tau_q = taus
+    lat = _lattice(tuple(e.shape), collision=collision, tau_f=tau_f, tau_v=tau_v, tau_e=tau_e,
+                   tau_eps=tau_eps, tau_q=tau_q, bc=bc, precision=precision)
+    lat.set_fields(e.cuda(), ux.cuda(), uy.cuda(), uz.cuda(), n.cuda())
+    lat.step(steps)
+    gpu = lat.fields("cuda")
+    tot = lat.totals()
+    prm = O.Params(collision=collision, tau_f=tau_f, tau_v=tau_v, tau_e=tau_e, tau_eps=tau_eps, tau_q=tau_q,
+                   bc=oracle_bc(bc))
+    f, g = O.init_populations(e, torch.stack([ux, uy, uz]), n)
+    f, g = O.run(f, g, prm, steps)
+    lat.close()
+    return gpu, oracle_fields(f, g), tot, O.conserved_totals(f, g)
+
+
+def _tube(L):
+    return [torch.from_numpy(a) for a in I.shock_tube(L)]
+
+
+# ----------------------------------------------------------------------------- shock tube (plain method)
+def test_shock_tube_bgk_fp64_2000_steps():
+    """400 x 1 x 1 shock tube, BGK tau = 0.9 for f and g, zero-gradient ends, 2000 steps."""
+    e, ux, uy, uz, n = _tube(400)
+    gpu, ref, _, _ = _run_both(e, ux, uy, uz, n, 2000, "bgk", (0.9, 0.9, 0.9, 0.9, 0.0),
+                               ("zero_gradient", "periodic", "periodic"))
+    err = field_errors(gpu, ref)
+    assert max(err.values()) < TOL64, err
+
+
+def test_shock_tube_mrt_fp64():
+    e, ux, uy, uz, n = _tube(333)
+    gpu, ref, _, _ = _run_both(e, ux, uy, uz, n, 700, "mrt", (0.6, 0.9, 0.55, 0.8, 0.0),
+                               ("zero_gradient", "periodic", "periodic"))
+    err = field_errors(gpu, ref)
+    assert max(err.values()) < TOL64, err
+
+
+# ----------------------------------------------------------------------------- 3-D boxes
+@pytest.mark.parametrize("collision, taus", [
+    ("mrt", (0.9, 0.9, 0.55, 0.8, 0.0)),
+    ("mrt", (0.7, 0.9, 0.6, 1.2, 1.4)),        # separate tau_q
+    ("bgk", (0.8, 0.9, 0.9, 0.9, 0.0)),
+])
+def test_periodic_box_ragged_fp64(collision, taus):
+    """Ragged 3-D box (several x-tiles plus a tail) with the seeded smooth fields."""
+    e, ux, uy, uz, n = I.periodic_box(None, seed=21, shape=(9, 11, 150))
+    gpu, ref, tot, tot_ref = _run_both(e, ux, uy, uz, n, 25, collision, taus, ("periodic",) * 3)
+    err = field_errors(gpu, ref)
+    assert max(err.values()) < TOL64, err
+    scale = [float(tot_ref[0])] + [float(tot_ref[1])] * 4
+    assert max(abs(a - float(b)) / s for a, b, s in zip(tot, tot_ref, scale)) < 1e-13
+
+
+def test_zero_gradient_all_axes_fp64():
+    e, ux, uy, uz, n = I.periodic_box(None, seed=22, shape=(7, 6, 37))
+    gpu, ref, _, _ = _run_both(e, 0.5 * ux, 0.5 * uy, 0.5 * uz, n, 30, "mrt", (0.9, 0.9, 0.55, 0.8, 0.0),
+                               ("zero_gradient",) * 3)
+    err = field_errors(gpu, ref)
+    assert max(err.values()) < TOL64, err
+
+
+def test_mixed_boundaries_fp64():
+    e, ux, uy, uz, n = I.periodic_box(None, seed=23, shape=(5, 8, 40))
+    gpu, ref, _, _ = _run_both(e, ux, uy, uz, n, 30, "mrt", (0.9, 0.9, 0.55, 0.8, 0.0),
+                               ("periodic", "zero_gradient", "periodic"))
+    err = field_errors(gpu, ref)
+    assert max(err.values()) < TOL64, err
+
+
+def test_single_node_and_thin_lattices():
+    """Degenerate extents: a 1 x 1 x 1 periodic node and 1-node-thick slabs."""
+    for shape in [(1, 1, 1), (1, 5, 1), (3, 1, 1), (2, 3, 129)]:
+        e, ux, uy, uz, n = I.periodic_box(None, seed=24, shape=shape)
+        gpu, ref, _, _ = _run_both(e, ux, uy, uz, n, 7, "mrt", (0.9, 0.9, 0.55, 0.8, 0.0), ("periodic",) * 3)
+        err = field_errors(gpu, ref)
+        assert max(err.values()) < TOL64, (shape, err)
+
+
+# ----------------------------------------------------------------------------- invariants
+def test_uniform_state_is_bitwise_uniform_on_gpu():
+    from paper_1211_3286_gb300.lattice import Lattice
+    sh = (6, 7, 130)
+    lat = Lattice(sh, collision="mrt", tau_f=0.7, tau_v=0.9, tau_e=0.55, tau_eps=0.8,
+                  bc=("zero_gradient", "periodic", "zero_gradient"))
+    one = torch.ones(sh, dtype=torch.float64, device="cuda")
+    lat.set_fields(0.012 * one, 0.2 * one, -0.1 * one, 0.05 * one, 0.8 * one)
+    lat.step(40)
+    s = lat.state()
+    assert torch.equal(s, s[:, :1, :1, :1].expand_as(s))
+    lat.close()
+
+
+def test_fields_round_trip_and_host_io():
+    from paper_1211_3286_gb300.lattice import Lattice
+    e, ux, uy, uz, n = I.periodic_box(None, seed=25, shape=(4, 5, 33))
+    lat = Lattice(tuple(e.shape), collision="mrt", tau_v=0.9, tau_e=0.55, tau_eps=0.8)
+    lat.set_fields(e, ux, uy, uz, n)          # host pointers
+    got = lat.fields("cpu")                   # host pointers
+    assert (got["e"] - e).abs().max() / e.max() < 1e-14
+    assert (got["ux"] - ux).abs().max() < 1e-14
+    assert (got["n"] - n).abs().max() / n.max() < 1e-14
+    st = lat.state("cpu")
+    lat.step(3)
+    lat.load_state(st)
+    assert torch.equal(lat.state("cpu"), st)
+    lat.close()
+
+
+def test_invalid_fields_are_rejected():
+    from paper_1211_3286_gb300 import _lib as L
+    from paper_1211_3286_gb300.lattice import Lattice
+    sh = (1, 1, 16)
+    lat = Lattice(sh)
+    one = torch.ones(sh, dtype=torch.float64)
+    e = 0.01 * one
+    e[0, 0, 5] = -1.0
+    with pytest.raises(L.RlbError) as ex:
+        lat.set_fields(e, 0 * one, 0 * one, 0 * one, one)
+    assert ex.value.code == L.RLB_EINVAL and "node 5" in str(ex.value)
+    ed = e.cuda()
+    with pytest.raises(L.RlbError) as ex:
+        lat.set_fields(ed, 0 * ed, 0 * ed, 0 * ed, 0 * ed + 1)
+    assert ex.value.code == L.RLB_EINVAL and "node 5" in str(ex.value)
+    lat.close()
+
+
+def test_nonphysical_state_is_flagged_not_faulted():
+    """A state whose node violates 4 T00^2 >= 3 |M|^2 is reported as RLB_ENONPHYS
+    with the node index; the context stays usable."""
+    from paper_1211_3286_gb300 import _lib as L
+    from paper_1211_3286_gb300.lattice import Lattice
+    sh = (1, 1, 32)
+    lat = Lattice(sh, collision="bgk", bc=("periodic",) * 3)
+    one = torch.ones(sh, dtype=torch.float64, device="cuda")
+    lat.set_fields(0.01 * one, 0 * one, 0 * one, 0 * one, one)
+    st = lat.state()
+    st[19 + 1, 0, 0, 7] = 1.0      # node 8 pulls +x from node 7 and -x from node 9:
+    st[19 + 2, 0, 0, 9] = -0.9     # there T00 ~ 0.1 while |M| ~ 1.9, so 4 T00^2 < 3 |M|^2
+    lat.load_state(st)
+    lat.step(1)
+    with pytest.raises(L.RlbError) as ex:
+        lat.check()
+    assert ex.value.code == L.RLB_ENONPHYS and "node 8" in str(ex.value)
+    lat.set_fields(0.01 * one, 0 * one, 0 * one, 0 * one, one)
+    lat.step(2)
+    lat.check()
+    lat.close()
+
+
+# ----------------------------------------------------------------------------- FP32 storage
+def test_fp32_storage_error_bound():
+    """FP32 populations (FP64 sums and recovery): stored values carry a relative
+    rounding of 2^-24 per step; after T steps of a dissipative scheme the field error
+    stays below a few T * 2^-24.  Bar used: 50 * 2^-24 * sqrt(T) with T = 60."""
+    e, ux, uy, uz, n = I.periodic_box(None, seed=26, shape=(8, 9, 70))
+    gpu, ref, tot, tot_ref = _run_both(e, ux, uy, uz, n, 60, "mrt", (0.9, 0.9, 0.55, 0.8, 0.0),
+                                       ("periodic",) * 3, precision="fp32")
+    err = field_errors(gpu, ref)
+    bound = 50 * 2.0 ** -24 * math.sqrt(60)
+    assert max(err.values()) < bound, err
+    assert max(err.values()) > 1e-12  # it really stored in FP32
+
+
+def test_fp32_storage_shock_tube():
+    e, ux, uy, uz, n = _tube(400)
+    gpu, ref, _, _ = _run_both(e, ux, uy, uz, n, 400, "mrt", (0.9, 0.9, 0.55, 0.8, 0.0),
+                               ("zero_gradient", "periodic", "periodic"), precision="fp32")
+    err = field_errors(gpu, ref)
+    assert max(err.values()) < 50 * 2.0 ** -24 * math.sqrt(400), err
+
+
+# ----------------------------------------------------------------------------- full size, sampled
+def _sampled_one_step(lat_state, next_state, shape, prm, K, seed):
+    """Oracle one-step update at K sampled nodes, from the GPU's state before the step."""
+    nz, ny, nx = shape
+    E, _ = O.d3q19()
+    rng = np.random.default_rng(seed)
+    idx = rng.integers(0, nz * ny * nx, size=K)
+    z, y, x = idx // (ny * nx), (idx // nx) % ny, idx % nx
+    f = torch.empty((19, K, 1, 1), dtype=torch.float64)
+    g = torch.empty((19, K, 1, 1), dtype=torch.float64)
+    st = lat_state
+    dev = st.device
+    for a in range(19):
+        cx, cy, cz = (int(E[a, 0]), int(E[a, 1]), int(E[a, 2]))
+        zs, ys, xs = (z - cz) % nz, (y - cy) % ny, (x - cx) % nx
+        zi, yi, xi = (torch.from_numpy(v).to(dev) for v in (zs, ys, xs))
+        f[a, :, 0, 0] = st[a][zi, yi, xi].double().cpu()
+        g[a, :, 0, 0] = st[19 + a][zi, yi, xi].double().cpu()
+    fo, go = O.collide(f, g, prm)
+    zi, yi, xi = (torch.from_numpy(v).to(dev) for v in (z, y, x))
+    nf = torch.stack([next_state[a][zi, yi, xi] for a in range(19)]).double().cpu()
+    ng = torch.stack([next_state[19 + a][zi, yi, xi] for a in range(19)]).double().cpu()
+    return fo.reshape(19, K), go.reshape(19, K), nf, ng
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_full_size_256_sampled_step_and_conservation(precision):
+    """256^3 MRT box (the benchmarked launch configuration): one step from the GPU
+    state at 4096 sampled nodes against the oracle's collide, and lattice-wide
+    conservation over 5 steps."""
+    from paper_1211_3286_gb300.lattice import Lattice
+    N = 256
+    e, ux, uy, uz, n = I.periodic_box(N, device="cuda")
+    lat = Lattice((N, N, N), collision="mrt", tau_f=0.9, tau_v=0.9, tau_e=0.55, tau_eps=0.8, precision=precision)
+    lat.set_fields(e, ux, uy, uz, n)
+    t0 = lat.totals()
+    lat.step(4)
+    s4 = lat.state()
+    lat.step(1)
+    s5 = lat.state()
+    t1 = lat.totals()
+    lat.check()
+    prm = O.Params(collision="mrt", tau_f=0.9, tau_v=0.9, tau_e=0.55, tau_eps=0.8)
+    fo, go, nf, ng = _sampled_one_step(s4, s5, (N, N, N), prm, 4096, 7)
+    if precision == "fp64":
+        assert ((go - ng).abs().max() / go.abs().max()) < 1e-14
+        assert ((fo - nf).abs().max() / fo.abs().max()) < 1e-14
+    else:
+        # the GPU rounds the outputs to FP32 and computes the relaxation in FP32
+        assert ((go - ng).abs().max() / go.abs().max()) < 4 * 2.0 ** -24
+        assert ((fo - nf).abs().max() / fo.abs().max()) < 4 * 2.0 ** -24
+    scale = [t0[0]] + [t0[1]] * 4
+    tol = 1e-13 if precision == "fp64" else 1e-6
+    assert max(abs(a - b) / s for a, b, s in zip(t1, t0, scale)) < tol
+    lat.close()
