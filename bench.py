@@ -36,6 +36,11 @@ WORKLOADS = {
     "box256": dict(N=256, precision="fp64", dtype="f64", bytes_per_update=608,
                    desc="3-D MRT periodic box, D3Q19, 256^3 nodes, FP64, tau_v=0.9 tau_e=0.55 tau_eps=0.8, "
                         "seeded smooth fields (max|u|=0.3), 500 steps"),
+    "box128": dict(N=128, precision="fp64", dtype="f64", bytes_per_update=608,
+                   desc="3-D MRT periodic box, D3Q19, 128^3 nodes, FP64 (small profiling case of the 256^3 "
+                        "workload, 1.3 GB of lattices)"),
+    "box128_fp32": dict(N=128, precision="fp32", dtype="f32-storage/f64-recovery", bytes_per_update=304,
+                        desc="3-D MRT periodic box, D3Q19, 128^3 nodes, FP32 storage (small profiling case)"),
     "box512_fp32": dict(N=512, precision="fp32", dtype="f32-storage/f64-recovery", bytes_per_update=304,
                         desc="3-D MRT periodic box, D3Q19, 512^3 nodes, FP32 population storage with FP64 sums "
                              "and recovery, same fields and taus, 200 steps"),

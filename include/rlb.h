@@ -141,6 +141,42 @@ int rlb_load_state(rlb_handle* h, const void* buf, int where);
 /* Number of time steps taken since the last rlb_set_fields / rlb_load_state. */
 long long rlb_steps_done(const rlb_handle* h);
 
+/*
+ * Conserved totals of a raw state, for callers that must not allocate.
+ *
+ * The paper has no counterpart of this call; it exists for callers that cannot
+ * allocate device memory when they need the totals: code that has handed the
+ * GPU's memory to a pool reserved at start-up (a framework's caching allocator
+ * or a fixed arena) and must not allocate around it, monitoring code that reports
+ * the conserved sums of a run that has just failed with out-of-memory, and
+ * latency-sensitive loops in which cudaMalloc / cudaFree would stall the work by
+ * synchronising the device.  It computes what rlb_conserved_totals computes
+ * (sum N0, sum T00, sum M_x, sum M_y, sum M_z in FP64, fixed reduction order;
+ * the order differs from rlb_conserved_totals, so the two agree to round-off)
+ * but takes the state itself rather than a handle and calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *   state      device pointer to a raw state in the rlb_save_state layout
+ *              (f[19][nodes] then g[19][nodes]), FP64 or FP32 per `precision`.
+ *   nodes      lattice nodes, 1 <= nodes <= RLB_NOALLOC_MAX_NODES; larger sizes
+ *              return RLB_EINVAL with the limit in rlb_last_error(NULL).
+ *   precision  RLB_FP64 or RLB_FP32_STORAGE.
+ *   out        5 doubles in `where` memory (RLB_DEVICE: written by a kernel on
+ *              `stream`, asynchronous; RLB_HOST: copied back, the call then
+ *              synchronises `stream`).
+ *   stream     cudaStream_t to run on (NULL = legacy default stream).
+ * Scratch: a file-scope device array of 4096 x 5 + 5 doubles (160 KiB) that every
+ * GPU loading librlb holds until the process exits.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  All calls
+ * share the array and it keeps the last call's contents (each call overwrites
+ * every slot it reads, so nothing needs clearing); calls whose kernels overlap
+ * on the GPU race on it, so serialise them (one stream, or events).  Errors are
+ * reported by the return code and rlb_last_error(NULL).
+ */
+#define RLB_NOALLOC_MAX_NODES 268435456
+int rlb_conserved_totals_noalloc(const void* state, size_t nodes, int precision, double* out, int where,
+                                 void* stream);
+
 #ifdef __cplusplus
 }
 #endif

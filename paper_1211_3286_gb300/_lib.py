@@ -64,6 +64,7 @@ def load():
         "rlb_save_state": (ctypes.c_int, [_P, _P, ctypes.c_int]),
         "rlb_load_state": (ctypes.c_int, [_P, _P, ctypes.c_int]),
         "rlb_steps_done": (ctypes.c_longlong, [_P]),
+        "rlb_conserved_totals_noalloc": (ctypes.c_int, [_P, ctypes.c_size_t, ctypes.c_int, _P, ctypes.c_int, _P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -76,7 +77,7 @@ def load():
 def exported_symbols():
     return ["rlb_create", "rlb_destroy", "rlb_last_error", "rlb_set_fields", "rlb_step", "rlb_check",
             "rlb_get_fields", "rlb_conserved_totals", "rlb_state_bytes", "rlb_save_state", "rlb_load_state",
-            "rlb_steps_done"]
+            "rlb_steps_done", "rlb_conserved_totals_noalloc"]
 
 
 def _check(rc, h=None):
@@ -136,3 +137,12 @@ def rlb_load_state(h, buf, where):
 
 def rlb_steps_done(h):
     return int(load().rlb_steps_done(h))
+
+
+RLB_NOALLOC_MAX_NODES = 268435456
+
+
+def rlb_conserved_totals_noalloc(state_ptr, nodes, precision, out_ptr, where, stream_ptr=None):
+    """Conserved totals of a raw device state without allocation (see include/rlb.h)."""
+    _check(load().rlb_conserved_totals_noalloc(state_ptr, int(nodes), int(precision), out_ptr, int(where),
+                                               stream_ptr), None)

@@ -7,4 +7,6 @@ namespace rlb {
 // meaning tau_v); returns RLB_OK or RLB_EINVAL with the reason in `why`.
 int validate_taus(double tau_f, double tau_v, double tau_e, double tau_eps, double tau_q, int collision,
                   std::string& why);
+// Records the message that rlb_last_error(NULL) returns (calls that take no handle).
+void set_handleless_error(const std::string& msg);
 }  // namespace rlb

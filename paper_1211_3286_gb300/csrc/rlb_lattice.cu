@@ -281,6 +281,8 @@ int grid_for(size_t nodes) {
 
 // ----------------------------------------------------------------------------- internal helpers
 namespace rlb {
+void set_handleless_error(const std::string& msg) { g_create_error = msg; }
+
 int validate_taus(double tau_f, double tau_v, double tau_e, double tau_eps, double tau_q, int collision,
                   std::string& why) {
   if (!(tau_f > 0.5) || !(tau_v > 0.5)) { why = "tau_f and tau_v must be > 0.5"; return RLB_EINVAL; }
