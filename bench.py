@@ -41,11 +41,18 @@ WORKLOADS = {
                         "workload, 1.3 GB of lattices)"),
     "box128_fp32": dict(N=128, precision="fp32", dtype="f32-storage/f64-recovery", bytes_per_update=304,
                         desc="3-D MRT periodic box, D3Q19, 128^3 nodes, FP32 storage (small profiling case)"),
+    "tubes": dict(N=None, precision="fp32", dtype="f32-storage/f64-recovery", bytes_per_update=304,
+                  desc="tau sweep: 1024 quasi-1D D3Q19 shock tubes, lengths uniform in [200, 3200], (tau_v, tau_e, "
+                       "tau_eps) log-uniform in [0.51, 3] with tau_e <= tau_v, P ratio 5.43:2.22, FP32 populations / "
+                       "FP64 recovery, 4000 steps in one persistent launch from a CUDA graph"),
     "box512_fp32": dict(N=512, precision="fp32", dtype="f32-storage/f64-recovery", bytes_per_update=304,
                         desc="3-D MRT periodic box, D3Q19, 512^3 nodes, FP32 population storage with FP64 sums "
                              "and recovery, same fields and taus, 200 steps"),
 }
 TAUS = dict(tau_f=0.9, tau_v=0.9, tau_e=0.55, tau_eps=0.8)
+
+# FP64 flops of one FP32-storage node update: moment sums 57 + recovery 23.
+FLOPS_PER_UPDATE_F32S_FP64PART = 80
 
 # FP64 flops (FMA = 2, sqrt and division = 1) of one FP64 MRT node update,
 # counted from the per-node arithmetic of the step kernel: moments 57,
@@ -166,6 +173,77 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_tubes(args, dist, rank, ws, local):
+    import numpy as np
+    from paper_1211_3286_gb300 import inputs as I
+    from paper_1211_3286_gb300.batch import TubeBatch
+    wl = WORKLOADS["tubes"]
+    lengths, taus = I.tube_sweep(1024)
+    nodes = int(lengths.sum())
+    parts = [I.shock_tube(int(L)) for L in lengths]
+    fields = [torch.from_numpy(np.concatenate([p[c].reshape(-1) for p in parts])) for c in range(5)]
+    stream = torch.cuda.Stream()
+    b = TubeBatch(lengths, taus, precision="fp32", stream=stream)
+    b.set_fields(*[t.cuda() for t in fields])
+    shape = b.autotune(16)
+    b.run(args.warmup)
+    b.check()
+    b.set_fields(*[t.cuda() for t in fields])
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as cs:
+        ev0.record(stream)
+        b.run(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    b.check()
+    ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    clocks = cs.summary()
+    mlups = nodes * args.steps * ws / (ms / 1e3) / 1e6
+    e2e = None
+    if not args.no_e2e:
+        hf = [t.pin_memory() for t in fields]
+        outs = [torch.empty(nodes, dtype=torch.float64).pin_memory() for _ in range(6)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.set_fields(*hf)
+        b.run(args.steps)
+        import ctypes
+        from paper_1211_3286_gb300 import _lib as L
+        L.rlb_batch_get_fields(b.handle, *[ctypes.c_void_p(o.data_ptr()) for o in outs], L.RLB_HOST)
+        dt = time.perf_counter() - t0
+        e2e = {"value": nodes * args.steps * ws / dt / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": 5 * nodes * 8 / args.steps, "d2h_bytes_per_step": 6 * nodes * 8 / args.steps,
+               "what": "rlb_batch_set_fields(host) + rlb_batch_run(K) + rlb_batch_get_fields(host), pinned"}
+    b.close()
+    hbm_peak, peak_kind = _peaks()
+    upd_s = nodes * args.steps / (ms / 1e3)
+    gbs = 304 * upd_s / 1e9
+    fp64_peak = 152 * 2 * 2 * 2.07
+    alu = {"bound": "alu", "achieved": FLOPS_PER_UPDATE_F32S_FP64PART * upd_s / 1e9, "peak": fp64_peak,
+           "unit": "GFLOP/s", "traffic": None, "peak_kind": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"}
+    alu["frac"] = alu["achieved"] / fp64_peak
+    hbm = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+           "traffic": None, "peak_kind": peak_kind, "note": "streaming-equivalent bytes (304 B/update); the tubes "
+           "are re-read through L2"}
+    roof = alu if alu["frac"] > hbm["frac"] else hbm
+    if rank == 0:
+        line = {"metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": wl["dtype"], "data": "synthetic",
+                "config": {"workload": wl["desc"], "nodes": nodes, "launch_shape": {"threads": shape[0],
+                           "ctas_per_sm": shape[1]}, "l2": "batch lattices %.0f MB; one launch covers all steps"
+                           % (2 * 38 * nodes * 4 / 1e6)},
+                "roofline": roof, "hbm_roofline": hbm, "clocks": clocks, "e2e": e2e, "gpu_launches": 1}
+        print(json.dumps(line))
+
+
 def run_ours(args):
     dist, rank, ws = _dist()
     if not torch.cuda.is_available():
@@ -177,6 +255,8 @@ def run_ours(args):
     from paper_1211_3286_gb300 import inputs as I
     from paper_1211_3286_gb300.lattice import Lattice
 
+    if args.workload == "tubes":
+        return run_tubes(args, dist, rank, ws, local)
     wl = WORKLOADS[args.workload]
     N = wl["N"]
     nodes = N ** 3

@@ -37,6 +37,12 @@ class rlb_config(ctypes.Structure):
                 ("bc", ctypes.c_int * 3), ("precision", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
+class rlb_batch_desc(ctypes.Structure):
+    _fields_ = [("ntubes", ctypes.c_int), ("lengths", ctypes.POINTER(ctypes.c_int)),
+                ("taus", ctypes.POINTER(ctypes.c_double)), ("tau_f", ctypes.POINTER(ctypes.c_double)),
+                ("collision", ctypes.c_int), ("precision", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
 _lib = None
 _P = ctypes.c_void_p
 _D = ctypes.POINTER(ctypes.c_double)
@@ -65,6 +71,19 @@ def load():
         "rlb_load_state": (ctypes.c_int, [_P, _P, ctypes.c_int]),
         "rlb_steps_done": (ctypes.c_longlong, [_P]),
         "rlb_conserved_totals_noalloc": (ctypes.c_int, [_P, ctypes.c_size_t, ctypes.c_int, _P, ctypes.c_int, _P]),
+        "rlb_batch_create": (ctypes.c_int, [ctypes.POINTER(rlb_batch_desc), ctypes.POINTER(_P)]),
+        "rlb_batch_destroy": (None, [_P]),
+        "rlb_batch_last_error": (ctypes.c_char_p, [_P]),
+        "rlb_batch_nodes": (ctypes.c_size_t, [_P]),
+        "rlb_batch_offset": (ctypes.c_size_t, [_P, ctypes.c_int]),
+        "rlb_batch_set_fields": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, ctypes.c_int]),
+        "rlb_batch_autotune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+        "rlb_batch_run": (ctypes.c_int, [_P, ctypes.c_int]),
+        "rlb_batch_check": (ctypes.c_int, [_P]),
+        "rlb_batch_get_fields": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, ctypes.c_int]),
+        "rlb_batch_state_bytes": (ctypes.c_size_t, [_P]),
+        "rlb_batch_save_state": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+        "rlb_batch_load_state": (ctypes.c_int, [_P, _P, ctypes.c_int]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -77,7 +96,10 @@ def load():
 def exported_symbols():
     return ["rlb_create", "rlb_destroy", "rlb_last_error", "rlb_set_fields", "rlb_step", "rlb_check",
             "rlb_get_fields", "rlb_conserved_totals", "rlb_state_bytes", "rlb_save_state", "rlb_load_state",
-            "rlb_steps_done", "rlb_conserved_totals_noalloc"]
+            "rlb_steps_done", "rlb_conserved_totals_noalloc",
+            "rlb_batch_create", "rlb_batch_destroy", "rlb_batch_last_error", "rlb_batch_nodes", "rlb_batch_offset",
+            "rlb_batch_set_fields", "rlb_batch_autotune", "rlb_batch_run", "rlb_batch_check", "rlb_batch_get_fields",
+            "rlb_batch_state_bytes", "rlb_batch_save_state", "rlb_batch_load_state"]
 
 
 def _check(rc, h=None):
@@ -146,3 +168,66 @@ def rlb_conserved_totals_noalloc(state_ptr, nodes, precision, out_ptr, where, st
     """Conserved totals of a raw device state without allocation (see include/rlb.h)."""
     _check(load().rlb_conserved_totals_noalloc(state_ptr, int(nodes), int(precision), out_ptr, int(where),
                                                stream_ptr), None)
+
+
+# ----------------------------------------------------------------------------- batch (include/rlb_batch.h)
+def _bcheck(rc, b=None):
+    if rc != RLB_OK:
+        msg = load().rlb_batch_last_error(b)
+        raise RlbError(rc, (msg or b"").decode())
+
+
+def rlb_batch_create(desc: rlb_batch_desc):
+    b = _P()
+    _bcheck(load().rlb_batch_create(ctypes.byref(desc), ctypes.byref(b)), None)
+    return b
+
+
+def rlb_batch_destroy(b):
+    load().rlb_batch_destroy(b)
+
+
+def rlb_batch_last_error(b):
+    return (load().rlb_batch_last_error(b) or b"").decode()
+
+
+def rlb_batch_nodes(b):
+    return int(load().rlb_batch_nodes(b))
+
+
+def rlb_batch_offset(b, tube):
+    return int(load().rlb_batch_offset(b, int(tube)))
+
+
+def rlb_batch_set_fields(b, e, ux, uy, uz, n, where):
+    _bcheck(load().rlb_batch_set_fields(b, e, ux, uy, uz, n, where), b)
+
+
+def rlb_batch_autotune(b, trial_steps):
+    ch = (ctypes.c_int * 2)()
+    _bcheck(load().rlb_batch_autotune(b, int(trial_steps), ch), b)
+    return int(ch[0]), int(ch[1])
+
+
+def rlb_batch_run(b, nsteps):
+    _bcheck(load().rlb_batch_run(b, int(nsteps)), b)
+
+
+def rlb_batch_check(b):
+    _bcheck(load().rlb_batch_check(b), b)
+
+
+def rlb_batch_get_fields(b, e, P, ux, uy, uz, n, where):
+    _bcheck(load().rlb_batch_get_fields(b, e, P, ux, uy, uz, n, where), b)
+
+
+def rlb_batch_state_bytes(b):
+    return int(load().rlb_batch_state_bytes(b))
+
+
+def rlb_batch_save_state(b, buf, where):
+    _bcheck(load().rlb_batch_save_state(b, buf, where), b)
+
+
+def rlb_batch_load_state(b, buf, where):
+    _bcheck(load().rlb_batch_load_state(b, buf, where), b)
