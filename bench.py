@@ -45,6 +45,10 @@ WORKLOADS = {
                   desc="tau sweep: 1024 quasi-1D D3Q19 shock tubes, lengths uniform in [200, 3200], (tau_v, tau_e, "
                        "tau_eps) log-uniform in [0.51, 3] with tau_e <= tau_v, P ratio 5.43:2.22, FP32 populations / "
                        "FP64 recovery, 4000 steps in one persistent launch from a CUDA graph"),
+    "adjoint": dict(N=None, precision="fp64", dtype="f64", bytes_per_update=608,
+                    desc="adjoint: quasi-1D D3Q19 shock tube of 1600 nodes, FP64 MRT (0.9, 0.55, 0.8), 4000 steps "
+                         "with sqrt(T) checkpoints; gradient of the P/u profile misfit w.r.t. tau_v, tau_e, "
+                         "tau_eps and the 1600-value initial e field (forward + recompute + reverse)"),
     "box512_fp32": dict(N=512, precision="fp32", dtype="f32-storage/f64-recovery", bytes_per_update=304,
                         desc="3-D MRT periodic box, D3Q19, 512^3 nodes, FP32 population storage with FP64 sums "
                              "and recovery, same fields and taus, 200 steps"),
@@ -244,6 +248,49 @@ def run_tubes(args, dist, rank, ws, local):
         print(json.dumps(line))
 
 
+def run_adjoint(args, dist, rank, ws, local):
+    from paper_1211_3286_gb300 import inputs as I
+    from paper_1211_3286_gb300.adjoint import misfit_gradient
+    from paper_1211_3286_gb300.lattice import Lattice
+    wl = WORKLOADS["adjoint"]
+    L, T = 1600, args.steps
+    zg = ("zero_gradient", "periodic", "periodic")
+    e, ux, uy, uz, n = (torch.from_numpy(a).cuda() for a in I.shock_tube(L))
+    pert = torch.from_numpy(I.perturbation(L)).reshape(1, 1, L).cuda()
+    stream = torch.cuda.Stream()
+    tgt = Lattice((1, 1, L), collision="mrt", tau_f=0.9, tau_v=0.909, tau_e=0.5555, tau_eps=0.808, bc=zg,
+                  stream=stream)
+    tgt.set_fields(e * (1 + 1e-3 * pert), ux, uy, uz, n)
+    tgt.step(T)
+    tf = tgt.fields("cuda")
+    tgt.close()
+    lat = Lattice((1, 1, L), collision="mrt", tau_f=0.9, tau_v=0.9, tau_e=0.55, tau_eps=0.8, bc=zg, stream=stream)
+
+    def one():
+        lat.set_fields(e, ux, uy, uz, n)
+        return misfit_gradient(lat, T, tf["P"], tf["ux"], tf["uy"], tf["uz"])
+    for _ in range(args.warmup):
+        one()
+    torch.cuda.synchronize()
+    reps = 3
+    with ClockSampler(local) as cs:
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            loss, dtau, de0 = one()
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / reps
+    lat.close()
+    if rank == 0:
+        line = {"metric": "MLUPS", "value": L * T / dt / 1e6, "unit": "MLUPS", "n_gpus": ws, "steps": T,
+                "warmup": args.warmup, "ms_per_step": dt * 1e3 / T, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": wl["desc"], "ms_per_gradient": dt * 1e3, "loss": loss,
+                           "dtau": dtau.tolist(), "value_counts": "forward node updates per second of a full "
+                           "gradient (forward + recompute + reverse)"},
+                "clocks": cs.summary(), "e2e": None, "gpu_launches": 5 * T}
+        print(json.dumps(line))
+
+
 def run_ours(args):
     dist, rank, ws = _dist()
     if not torch.cuda.is_available():
@@ -257,6 +304,8 @@ def run_ours(args):
 
     if args.workload == "tubes":
         return run_tubes(args, dist, rank, ws, local)
+    if args.workload == "adjoint":
+        return run_adjoint(args, dist, rank, ws, local)
     wl = WORKLOADS[args.workload]
     N = wl["N"]
     nodes = N ** 3

@@ -366,4 +366,6 @@ def misfit_and_gradient(e0, u0, n0, prm: Params, nsteps, P_target, u_target, w_P
     f, g = run(f, g, q, nsteps, check=False)
     loss = profile_misfit(f, g, P_target, u_target, w_P, w_u)
     loss.backward()
-    return (float(loss.detach()), torch.stack([tv.grad, te.grad, tp.grad]).detach(), e0.grad.detach())
+    # a relaxation time the collision does not use (tau_e, tau_eps under BGK) has no gradient
+    grads = [t.grad if t.grad is not None else torch.zeros((), dtype=DT) for t in (tv, te, tp)]
+    return (float(loss.detach()), torch.stack(grads).detach(), e0.grad.detach())

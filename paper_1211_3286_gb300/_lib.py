@@ -84,6 +84,8 @@ def load():
         "rlb_batch_state_bytes": (ctypes.c_size_t, [_P]),
         "rlb_batch_save_state": (ctypes.c_int, [_P, _P, ctypes.c_int]),
         "rlb_batch_load_state": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+        "rlb_adjoint": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_int, _D, _D, _P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -99,7 +101,7 @@ def exported_symbols():
             "rlb_steps_done", "rlb_conserved_totals_noalloc",
             "rlb_batch_create", "rlb_batch_destroy", "rlb_batch_last_error", "rlb_batch_nodes", "rlb_batch_offset",
             "rlb_batch_set_fields", "rlb_batch_autotune", "rlb_batch_run", "rlb_batch_check", "rlb_batch_get_fields",
-            "rlb_batch_state_bytes", "rlb_batch_save_state", "rlb_batch_load_state"]
+            "rlb_batch_state_bytes", "rlb_batch_save_state", "rlb_batch_load_state", "rlb_adjoint"]
 
 
 def _check(rc, h=None):
@@ -231,3 +233,13 @@ def rlb_batch_save_state(b, buf, where):
 
 def rlb_batch_load_state(b, buf, where):
     _bcheck(load().rlb_batch_load_state(b, buf, where), b)
+
+
+# ----------------------------------------------------------------------------- adjoint (include/rlb_adjoint.h)
+def rlb_adjoint(h, nsteps, checkpoint_every, target_P, target_ux, target_uy, target_uz, w_P, w_u, where, de0_ptr):
+    """Returns (loss, [dJ/dtau_v, dJ/dtau_e, dJ/dtau_eps]); de0 is written to de0_ptr when given."""
+    loss = ctypes.c_double()
+    dtau = (ctypes.c_double * 3)()
+    _check(load().rlb_adjoint(h, int(nsteps), int(checkpoint_every), target_P, target_ux, target_uy, target_uz,
+                              float(w_P), float(w_u), int(where), ctypes.byref(loss), dtau, de0_ptr), h)
+    return loss.value, list(dtau)

@@ -1,0 +1,475 @@
+// rlb_adjoint.cu -- reverse-mode (adjoint) kernels of the fused step and the
+// checkpointed driver rlb_adjoint (include/rlb_adjoint.h).
+//
+// Per step the forward map is g^{t+1} = C(h; omega), h = S g^t, with S the pull
+// stream and C the per-node g collide of rlb_node.cuh (FP64).  The adjoint step
+// computes, per node, mu = C_h^T lambda^{t+1} and omega_bar += C_omega^T lambda^{t+1}
+// (the forward intermediates are recomputed from h, then the chain is walked
+// backwards by hand), and then lambda^t = S^T mu by a gather: the adjoint of
+// "node x pulls link a from src(x)" is "node y collects link a from every x with
+// src(x) = y" -- one node for a periodic axis, and for a zero-gradient axis also
+// the edge node's own clamped pull.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/rlb.h"
+#include "../../include/rlb_adjoint.h"
+#include "rlb_internal.h"
+#include "rlb_node.cuh"
+
+using namespace rlb;
+
+namespace {
+
+constexpr int kThreads = 128;
+
+struct AGeo {
+  int nx, ny, nz;
+  int zgx, zgy, zgz;
+  unsigned long long n;
+};
+
+__device__ __forceinline__ int pull_src(int i, int c, int n, int zg) {
+  int s = i - c;
+  if (s < 0) s = zg ? 0 : n - 1;
+  if (s >= n) s = zg ? n - 1 : 0;
+  return s;
+}
+
+// Nodes x of one axis whose pull with offset c lands on i (at most two).
+__device__ __forceinline__ int preimages(int i, int c, int n, int zg, int (&x)[2]) {
+  if (c == 0) { x[0] = i; return 1; }
+  if (!zg) { int v = i + c; if (v < 0) v += n; if (v >= n) v -= n; x[0] = v; return 1; }
+  int k = 0;
+  if (i + c >= 0 && i + c < n) x[k++] = i + c;
+  if ((c == 1 && i == 0) || (c == -1 && i == n - 1)) x[k++] = i;
+  return k;
+}
+
+struct GFwd {
+  double sp[9], dp[9], Sa, Sd, T00, Mx, My, Mz, MM, A, sA, sigma, is, ux, uy, uz, P, u2, su2, P3, kg, geq0;
+  double n0, nA, nD, ne, np, cu[9];
+};
+
+__device__ __forceinline__ void gforward(const double (&h)[19], const StepConst& k, bool mrt, GFwd& F) {
+#pragma unroll
+  for (int p = 0; p < 9; ++p) {
+    F.sp[p] = h[2 * p + 1] + h[2 * p + 2];
+    F.dp[p] = h[2 * p + 1] - h[2 * p + 2];
+  }
+  F.Sa = (F.sp[0] + F.sp[1]) + F.sp[2];
+  F.Sd = ((F.sp[3] + F.sp[4]) + (F.sp[5] + F.sp[6])) + (F.sp[7] + F.sp[8]);
+  F.T00 = (h[0] + F.Sa) + F.Sd;
+  F.Mx = ((F.dp[0] + F.dp[3]) + (F.dp[4] + F.dp[5])) + F.dp[6];
+  F.My = ((F.dp[1] + F.dp[3]) - (F.dp[4] - F.dp[7])) + F.dp[8];
+  F.Mz = ((F.dp[2] + F.dp[5]) - (F.dp[6] - F.dp[7])) - F.dp[8];
+  F.MM = fma(F.Mx, F.Mx, fma(F.My, F.My, F.Mz * F.Mz));
+  F.A = fma(4.0 * F.T00, F.T00, -3.0 * F.MM);
+  F.sA = sqrt(F.A);
+  F.sigma = fma(2.0, F.T00, F.sA) * (1.0 / 3.0);
+  F.is = 1.0 / F.sigma;
+  F.ux = F.Mx * F.is;
+  F.uy = F.My * F.is;
+  F.uz = F.Mz * F.is;
+  F.P = F.sigma - F.T00;
+  F.u2 = fma(F.ux, F.ux, fma(F.uy, F.uy, F.uz * F.uz));
+  F.su2 = F.sigma * F.u2;
+  F.P3 = 3.0 * F.P;
+  F.kg = fma(-1.5, F.su2, F.P3);
+  F.geq0 = fma(-0.5, F.su2, F.sigma - F.P3);
+  pair_cu<double>(F.ux, F.uy, F.uz, F.cu);
+  if (mrt) {
+    F.n0 = h[0] - F.geq0;
+    F.nA = F.Sa - F.P;
+    F.nD = fma(-0.5, F.su2, F.Sd - F.P);
+    F.ne = fma(8.0, F.nD, fma(-11.0, F.nA, -30.0 * F.n0));
+    F.np = fma(-4.0, F.nA, fma(12.0, F.n0, F.nD));
+  }
+}
+
+// Reverse of the recovery + moments given cotangents of (sigma, P via Pb, u, T00):
+// accumulates into hb.
+__device__ __forceinline__ void recovery_moments_reverse(const GFwd& F, double sigmab, double Pb, double uxb,
+                                                         double uyb, double uzb, double T00b, double Sab, double Sdb,
+                                                         double h0b_extra, double (&hb)[19]) {
+  // P = sigma - T00
+  sigmab += Pb;
+  T00b -= Pb;
+  // u = M * is
+  double Mxb = F.is * uxb, Myb = F.is * uyb, Mzb = F.is * uzb;
+  const double isb = F.Mx * uxb + F.My * uyb + F.Mz * uzb;
+  // is = 1 / sigma
+  sigmab -= F.is * F.is * isb;
+  // sigma = (2 T00 + sA) / 3
+  T00b += (2.0 / 3.0) * sigmab;
+  const double sAb = sigmab * (1.0 / 3.0);
+  // sA = sqrt(A)
+  const double Ab = sAb * 0.5 / F.sA;
+  // A = 4 T00^2 - 3 MM
+  T00b += 8.0 * F.T00 * Ab;
+  const double MMb = -3.0 * Ab;
+  Mxb += 2.0 * F.Mx * MMb;
+  Myb += 2.0 * F.My * MMb;
+  Mzb += 2.0 * F.Mz * MMb;
+  // T00 = h0 + Sa + Sd ; Sa, Sd from pair sums ; M from pair differences
+  Sab += T00b;
+  Sdb += T00b;
+  hb[0] += T00b + h0b_extra;
+  double dpb[9];
+  dpb[0] = Mxb; dpb[1] = Myb; dpb[2] = Mzb;
+  dpb[3] = Mxb + Myb; dpb[4] = Mxb - Myb;
+  dpb[5] = Mxb + Mzb; dpb[6] = Mxb - Mzb;
+  dpb[7] = Myb + Mzb; dpb[8] = Myb - Mzb;
+#pragma unroll
+  for (int p = 0; p < 9; ++p) {
+    const double spb = p < 3 ? Sab : Sdb;
+    hb[2 * p + 1] += spb + dpb[p];
+    hb[2 * p + 2] += spb - dpb[p];
+  }
+}
+
+// Vector-Jacobian product of the g collide: given h (pulled) and lo (cotangent of
+// the post-collision g), returns hb = C_h^T lo and the omega cotangents.
+template <bool MRT>
+__device__ __forceinline__ void g_collide_vjp(const double (&h)[19], const double (&lo)[19], const StepConst& k,
+                                              double (&hb)[19], double& wvb, double& web, double& wpb) {
+  GFwd F;
+  gforward(h, k, MRT, F);
+  const double om = k.omv, om1 = k.omv1;
+  const double wA = 1.0 / 18.0, wD = 1.0 / 36.0;
+  double SAb = 0, SDb = 0, AAb = 0, ADb = 0, KAb = 0, KDb = 0, cub[9];
+  const double SA = k.gA_s * F.sigma, SD = k.gD_s * F.sigma, AA = k.gA_a * F.sigma, AD = k.gD_a * F.sigma;
+  wvb = 0;
+  web = 0;
+  wpb = 0;
+#pragma unroll
+  for (int p = 0; p < 9; ++p) {
+    const double la = lo[2 * p + 1], lb = lo[2 * p + 2];
+    hb[2 * p + 1] = om1 * la;
+    hb[2 * p + 2] = om1 * lb;
+    wvb -= h[2 * p + 1] * la + h[2 * p + 2] * lb;
+    const double evb = la + lb, odb = la - lb;
+    const double c = F.cu[p];
+    if (p < 3) {
+      SAb += evb * c * c; KAb += evb; AAb += odb * c;
+      cub[p] = evb * 2.0 * SA * c + odb * AA;
+    } else {
+      SDb += evb * c * c; KDb += evb; ADb += odb * c;
+      cub[p] = evb * 2.0 * SD * c + odb * AD;
+    }
+  }
+  // rest link: out0 = (1 - om) h0 + om geq0 (+ 30 ae - 12 ap)
+  const double l0 = lo[0];
+  hb[0] = om1 * l0;
+  wvb += (F.geq0 - h[0]) * l0;
+  double geq0b = om * l0;
+  double aeb = 30.0 * l0, apb = -12.0 * l0;
+  // K_A = om wA kg + 11 ae + 4 ap ; K_D = om wD kg - 8 ae - ap
+  aeb += 11.0 * KAb - 8.0 * KDb;
+  apb += 4.0 * KAb - KDb;
+  const double kgb = om * (wA * KAb + wD * KDb);
+  wvb += F.kg * (wA * KAb + wD * KDb);
+  // S = 4.5 om w sigma, A = 3 om w sigma
+  double sigmab = om * (4.5 * (wA * SAb + wD * SDb) + 3.0 * (wA * AAb + wD * ADb));
+  wvb += F.sigma * (4.5 * (wA * SAb + wD * SDb) + 3.0 * (wA * AAb + wD * ADb));
+  double Sab = 0, Sdb = 0, Pb = 0, su2b = 0, h0x = 0;
+  if (MRT) {
+    const double neb = k.ce * aeb, npb = k.cp * apb;
+    const double ceb = F.ne * aeb, cpb = F.np * apb;
+    web += ceb / 2394.0;
+    wpb += cpb / 252.0;
+    wvb -= ceb / 2394.0 + cpb / 252.0;
+    const double n0b = -30.0 * neb + 12.0 * npb;
+    const double nAb = -11.0 * neb - 4.0 * npb;
+    const double nDb = 8.0 * neb + npb;
+    h0x += n0b;
+    geq0b -= n0b;
+    Sab += nAb;
+    Pb -= nAb;
+    Sdb += nDb;
+    Pb -= nDb;
+    su2b -= 0.5 * nDb;
+  }
+  // geq0 = sigma - P3 - 0.5 su2 ; kg = P3 - 1.5 su2 ; P3 = 3 P ; su2 = sigma u2
+  sigmab += geq0b;
+  double P3b = -geq0b + kgb;
+  su2b += -0.5 * geq0b - 1.5 * kgb;
+  Pb += 3.0 * P3b;
+  sigmab += F.u2 * su2b;
+  const double u2b = F.sigma * su2b;
+  // cu_p = c_p . u ; u2 = |u|^2
+  double uxb = ((cub[0] + cub[3]) + (cub[4] + cub[5])) + cub[6];
+  double uyb = ((cub[1] + cub[3]) - (cub[4] - cub[7])) + cub[8];
+  double uzb = ((cub[2] + cub[5]) - (cub[6] - cub[7])) - cub[8];
+  uxb += 2.0 * F.ux * u2b;
+  uyb += 2.0 * F.uy * u2b;
+  uzb += 2.0 * F.uz * u2b;
+  recovery_moments_reverse(F, sigmab, Pb, uxb, uyb, uzb, 0.0, Sab, Sdb, h0x, hb);
+}
+
+template <bool MRT>
+__global__ void __launch_bounds__(kThreads) k_adj_collide(const double* __restrict__ g, const double* __restrict__ lam,
+                                                         double* __restrict__ mu, double* __restrict__ tb, AGeo geo,
+                                                         StepConst k) {
+  const unsigned long long i = blockIdx.x * (unsigned long long)kThreads + threadIdx.x;
+  if (i >= geo.n) return;
+  const int x = (int)(i % geo.nx), y = (int)((i / geo.nx) % geo.ny), z = (int)(i / ((unsigned long long)geo.nx * geo.ny));
+  double h[19], lo[19], hb[19];
+#pragma unroll
+  for (int a = 0; a < 19; ++a) {
+    const int xs = pull_src(x, link_cx(a), geo.nx, geo.zgx);
+    const int ys = pull_src(y, link_cy(a), geo.ny, geo.zgy);
+    const int zs = pull_src(z, link_cz(a), geo.nz, geo.zgz);
+    const unsigned long long s = ((unsigned long long)zs * geo.ny + ys) * geo.nx + xs;
+    h[a] = g[(unsigned long long)a * geo.n + s];
+    lo[a] = lam[(unsigned long long)a * geo.n + i];
+  }
+  double wvb, web, wpb;
+  g_collide_vjp<MRT>(h, lo, k, hb, wvb, web, wpb);
+#pragma unroll
+  for (int a = 0; a < 19; ++a) mu[(unsigned long long)a * geo.n + i] = hb[a];
+  tb[i] += wvb;
+  tb[geo.n + i] += web;
+  tb[2 * geo.n + i] += wpb;
+}
+
+__global__ void __launch_bounds__(kThreads) k_adj_stream(const double* __restrict__ mu, double* __restrict__ lam,
+                                                        AGeo geo) {
+  const unsigned long long i = blockIdx.x * (unsigned long long)kThreads + threadIdx.x;
+  if (i >= geo.n) return;
+  const int x = (int)(i % geo.nx), y = (int)((i / geo.nx) % geo.ny), z = (int)(i / ((unsigned long long)geo.nx * geo.ny));
+#pragma unroll
+  for (int a = 0; a < 19; ++a) {
+    int px[2], py[2], pz[2];
+    const int nxp = preimages(x, link_cx(a), geo.nx, geo.zgx, px);
+    const int nyp = preimages(y, link_cy(a), geo.ny, geo.zgy, py);
+    const int nzp = preimages(z, link_cz(a), geo.nz, geo.zgz, pz);
+    double acc = 0.0;
+    for (int iz = 0; iz < nzp; ++iz)
+      for (int iy = 0; iy < nyp; ++iy)
+        for (int ix = 0; ix < nxp; ++ix)
+          acc += mu[(unsigned long long)a * geo.n + ((unsigned long long)pz[iz] * geo.ny + py[iy]) * geo.nx + px[ix]];
+    lam[(unsigned long long)a * geo.n + i] = acc;
+  }
+}
+
+// lambda^T = dJ/dg^T and the per-node misfit.
+__global__ void __launch_bounds__(kThreads) k_adj_loss(const double* __restrict__ g, const double* __restrict__ tP,
+                                                      const double* __restrict__ tux, const double* __restrict__ tuy,
+                                                      const double* __restrict__ tuz, double wP, double wu,
+                                                      double* __restrict__ lam, double* __restrict__ lossn,
+                                                      unsigned long long n) {
+  const unsigned long long i = blockIdx.x * (unsigned long long)kThreads + threadIdx.x;
+  if (i >= n) return;
+  double h[19], hb[19];
+#pragma unroll
+  for (int a = 0; a < 19; ++a) {
+    h[a] = g[(unsigned long long)a * n + i];
+    hb[a] = 0.0;
+  }
+  GFwd F;
+  StepConst dummy{};
+  gforward(h, dummy, false, F);
+  const double rP = F.P - tP[i], rx = F.ux - tux[i], ry = F.uy - tuy[i], rz = F.uz - tuz[i];
+  lossn[i] = wP * rP * rP + wu * (rx * rx + ry * ry + rz * rz);
+  recovery_moments_reverse(F, 0.0, 2.0 * wP * rP, 2.0 * wu * rx, 2.0 * wu * ry, 2.0 * wu * rz, 0.0, 0.0, 0.0, 0.0,
+                           hb);
+#pragma unroll
+  for (int a = 0; a < 19; ++a) lam[(unsigned long long)a * n + i] = hb[a];
+}
+
+// dJ/de0 of an equilibrium initial state: g^0 is linear in e0, so sum_a lambda_a g0_a / e0.
+__global__ void __launch_bounds__(kThreads) k_adj_e0(const double* __restrict__ g0, const double* __restrict__ lam,
+                                                    double* __restrict__ de0, unsigned long long n) {
+  const unsigned long long i = blockIdx.x * (unsigned long long)kThreads + threadIdx.x;
+  if (i >= n) return;
+  double h[19];
+  double acc = 0.0;
+#pragma unroll
+  for (int a = 0; a < 19; ++a) {
+    h[a] = g0[(unsigned long long)a * n + i];
+    acc = fma(lam[(unsigned long long)a * n + i], h[a], acc);
+  }
+  GFwd F;
+  StepConst dummy{};
+  gforward(h, dummy, false, F);
+  de0[i] = acc / (3.0 * F.P);
+}
+
+// Deterministic sums of `rows` arrays of length n (one block per row).
+__global__ void __launch_bounds__(256) k_rowsum(const double* __restrict__ a, unsigned long long n,
+                                                double* __restrict__ out) {
+  __shared__ double sh[256];
+  double acc = 0.0;
+  const double* r = a + blockIdx.x * n;
+  for (unsigned long long i = threadIdx.x; i < n; i += 256) acc += r[i];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = sh[0];
+}
+
+int afail(rlb_handle* h, int code, const std::string& m) {
+  h->err = m;
+  return code;
+}
+
+struct DevBufs {
+  std::vector<void*> ptrs;
+  ~DevBufs() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+  bool get(void** p, size_t bytes) {
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      *p = nullptr;
+      return false;
+    }
+    ptrs.push_back(*p);
+    return true;
+  }
+};
+
+}  // namespace
+
+extern "C" int rlb_adjoint(rlb_handle* h, int nsteps, int checkpoint_every, const double* target_P,
+                           const double* target_ux, const double* target_uy, const double* target_uz, double w_P,
+                           double w_u, int where, double* loss, double* dtau, double* de0) {
+  if (!h) return RLB_EINVAL;
+  if (nsteps < 0) return afail(h, RLB_EINVAL, "nsteps must be >= 0");
+  if (!target_P || !target_ux || !target_uy || !target_uz || !loss || !dtau)
+    return afail(h, RLB_EINVAL, "null argument");
+  if (where != RLB_HOST && where != RLB_DEVICE) return afail(h, RLB_EINVAL, "where must be RLB_HOST or RLB_DEVICE");
+  if (h->esize != 8) return afail(h, RLB_EINVAL, "rlb_adjoint needs an RLB_FP64 lattice");
+  if (h->cfg.collision == RLB_MRT && h->cfg.tau_q > 0 && h->cfg.tau_q != h->cfg.tau_v)
+    return afail(h, RLB_EINVAL, "rlb_adjoint needs tau_q tied to tau_v (tau_q <= 0)");
+  const bool mrt = h->cfg.collision == RLB_MRT;
+  const unsigned long long N = h->nodes;
+  const size_t state_bytes = 38 * N * sizeof(double), gbytes = 19 * N * sizeof(double);
+  const int K = checkpoint_every > 0 ? checkpoint_every : std::max(1, (int)std::ceil(std::sqrt((double)nsteps)));
+  const int nseg = nsteps > 0 ? (nsteps + K - 1) / K : 0;
+  cudaStream_t st = h->stream;
+
+  DevBufs mem;
+  std::vector<void*> ckpt(nseg, nullptr), seg(K + 1, nullptr);
+  double *lam = nullptr, *mu = nullptr, *tb = nullptr, *lossn = nullptr, *sums = nullptr, *tgt = nullptr;
+  double* dde0 = nullptr;
+  bool ok = true;
+  for (int s = 0; s < nseg && ok; ++s) ok = mem.get(&ckpt[s], state_bytes);
+  for (int j = 0; j <= K && ok && nsteps > 0; ++j) ok = mem.get(&seg[j], state_bytes);
+  ok = ok && mem.get((void**)&lam, gbytes) && mem.get((void**)&mu, gbytes) &&
+       mem.get((void**)&tb, 3 * N * sizeof(double)) && mem.get((void**)&lossn, N * sizeof(double)) &&
+       mem.get((void**)&sums, 8 * sizeof(double)) && mem.get((void**)&dde0, N * sizeof(double));
+  void* g0copy = nullptr;
+  ok = ok && mem.get(&g0copy, state_bytes);
+  if (ok && where == RLB_HOST) ok = mem.get((void**)&tgt, 4 * N * sizeof(double));
+  if (!ok) return afail(h, RLB_ENOMEM, "cannot allocate adjoint checkpoints and buffers");
+
+#define ACUDA(call)                                                                       \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) return afail(h, RLB_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+  const double* tP = target_P;
+  const double *tx = target_ux, *ty = target_uy, *tz = target_uz;
+  if (where == RLB_HOST) {
+    const double* src[4] = {target_P, target_ux, target_uy, target_uz};
+    for (int c = 0; c < 4; ++c)
+      ACUDA(cudaMemcpyAsync(tgt + c * N, src[c], N * sizeof(double), cudaMemcpyHostToDevice, st));
+    tP = tgt; tx = tgt + N; ty = tgt + 2 * N; tz = tgt + 3 * N;
+  }
+  AGeo geo{h->cfg.nx, h->cfg.ny, h->cfg.nz, h->cfg.bc[0] == RLB_ZERO_GRADIENT, h->cfg.bc[1] == RLB_ZERO_GRADIENT,
+           h->cfg.bc[2] == RLB_ZERO_GRADIENT, N};
+  const unsigned grid = (unsigned)((N + kThreads - 1) / kThreads);
+
+  // ---- forward with checkpoints
+  ACUDA(cudaMemcpyAsync(g0copy, h->lat[h->cur], state_bytes, cudaMemcpyDeviceToDevice, st));
+  for (int t = 0; t < nsteps; ++t) {
+    if (t % K == 0) ACUDA(cudaMemcpyAsync(ckpt[t / K], h->lat[h->cur], state_bytes, cudaMemcpyDeviceToDevice, st));
+    ACUDA(enqueue_steps(h, 1, st));
+  }
+  {
+    ACUDA(cudaStreamSynchronize(st));
+    unsigned long long bad = ~0ull;
+    ACUDA(cudaMemcpy(&bad, h->d_bad, sizeof bad, cudaMemcpyDeviceToHost));
+    if (bad != ~0ull) {
+      const unsigned long long none = ~0ull;
+      ACUDA(cudaMemcpy(h->d_bad, &none, sizeof none, cudaMemcpyHostToDevice));
+      char buf[128];
+      std::snprintf(buf, sizeof buf, "non-physical state at node %llu during the forward run", bad);
+      return afail(h, RLB_ENONPHYS, buf);
+    }
+  }
+  void* final_state = h->lat[h->cur];
+  const long long steps_before = h->steps;
+  // ---- loss and lambda^T
+  const double* gT = (const double*)final_state + 19 * N;
+  k_adj_loss<<<grid, kThreads, 0, st>>>(gT, tP, tx, ty, tz, w_P, w_u, lam, lossn, N);
+  ACUDA(cudaGetLastError());
+  ACUDA(cudaMemsetAsync(tb, 0, 3 * N * sizeof(double), st));
+
+  // ---- backward over segments, recomputing each segment from its checkpoint
+  void* saved_lat[2] = {h->lat[0], h->lat[1]};
+  const int saved_cur = h->cur;
+  for (int s = nseg - 1; s >= 0; --s) {
+    const int t0 = s * K, t1 = std::min(nsteps, t0 + K);
+    ACUDA(cudaMemcpyAsync(seg[0], ckpt[s], state_bytes, cudaMemcpyDeviceToDevice, st));
+    for (int j = 0; j + 1 < t1 - t0; ++j) {   // seg[j] holds g^{t0 + j}
+      h->lat[0] = seg[j];
+      h->lat[1] = seg[j + 1];
+      h->cur = 0;
+      cudaError_t e = enqueue_steps(h, 1, st);
+      if (e != cudaSuccess) {
+        h->lat[0] = saved_lat[0]; h->lat[1] = saved_lat[1]; h->cur = saved_cur;
+        return afail(h, RLB_ECUDA, std::string("recompute: ") + cudaGetErrorString(e));
+      }
+    }
+    for (int t = t1 - 1; t >= t0; --t) {
+      const double* gt = (const double*)seg[t - t0] + 19 * N;
+      if (mrt) k_adj_collide<true><<<grid, kThreads, 0, st>>>(gt, lam, mu, tb, geo, h->k);
+      else k_adj_collide<false><<<grid, kThreads, 0, st>>>(gt, lam, mu, tb, geo, h->k);
+      k_adj_stream<<<grid, kThreads, 0, st>>>(mu, lam, geo);
+    }
+  }
+  h->lat[0] = saved_lat[0];
+  h->lat[1] = saved_lat[1];
+  h->cur = saved_cur;
+  h->steps = steps_before;
+  ACUDA(cudaGetLastError());
+  if (h->lat[h->cur] != final_state) return afail(h, RLB_ECUDA, "internal: lattice bookkeeping");
+
+  // ---- dJ/de0, sums
+  k_adj_e0<<<grid, kThreads, 0, st>>>((const double*)g0copy + 19 * N, lam, dde0, N);
+  k_rowsum<<<3, 256, 0, st>>>(tb, N, sums);
+  k_rowsum<<<1, 256, 0, st>>>(lossn, N, sums + 3);
+  ACUDA(cudaGetLastError());
+  double hs[4];
+  ACUDA(cudaMemcpyAsync(hs, sums, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (de0)
+    ACUDA(cudaMemcpyAsync(de0, dde0, N * sizeof(double),
+                          where == RLB_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+  ACUDA(cudaStreamSynchronize(st));
+  // omega = 1 / tau  =>  dJ/dtau = -omega^2 dJ/domega
+  const double wv = 1.0 / h->cfg.tau_v;
+  *loss = hs[3];
+  dtau[0] = -wv * wv * hs[0];
+  if (mrt) {
+    const double we = 1.0 / h->cfg.tau_e, wp = 1.0 / h->cfg.tau_eps;
+    dtau[1] = -we * we * hs[1];
+    dtau[2] = -wp * wp * hs[2];
+  } else {
+    dtau[1] = 0.0;
+    dtau[2] = 0.0;
+  }
+  return RLB_OK;
+#undef ACUDA
+}

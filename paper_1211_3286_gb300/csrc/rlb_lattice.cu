@@ -24,21 +24,6 @@
 
 using namespace rlb;
 
-struct rlb_handle {
-  rlb_config cfg;
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  size_t nodes = 0;
-  size_t esize = 8;
-  void* lat[2] = {nullptr, nullptr};
-  int cur = 0;
-  unsigned long long* d_bad = nullptr;   // smallest non-physical node index, ULLONG_MAX if none
-  double* d_part = nullptr;              // reduction partials
-  double* d_stage = nullptr;             // 6 x nodes FP64 staging for host field I/O
-  StepConst k{};
-  long long steps = 0;
-  std::string err;
-};
 
 namespace {
 
@@ -179,15 +164,15 @@ Geo make_geo(const rlb_handle* h) {
 bool qsep(const rlb_config& c) { return c.collision == RLB_MRT && c.tau_q > 0 && c.tau_q != c.tau_v; }
 
 template <typename S>
-cudaError_t launch_step(rlb_handle* h, const void* src, void* dst) {
+cudaError_t launch_step(rlb_handle* h, const void* src, void* dst, cudaStream_t st) {
   const Geo geo = make_geo(h);
   dim3 grid((geo.nx + kBlockX - 1) / kBlockX, geo.ny, geo.nz);
   const bool mrt = h->cfg.collision == RLB_MRT, q = qsep(h->cfg);
   const S* s = (const S*)src;
   S* d = (S*)dst;
-  if (!mrt) k_step<S, false, false><<<grid, kBlockX, 0, h->stream>>>(s, d, geo, h->k, h->d_bad);
-  else if (!q) k_step<S, true, false><<<grid, kBlockX, 0, h->stream>>>(s, d, geo, h->k, h->d_bad);
-  else k_step<S, true, true><<<grid, kBlockX, 0, h->stream>>>(s, d, geo, h->k, h->d_bad);
+  if (!mrt) k_step<S, false, false><<<grid, kBlockX, 0, st>>>(s, d, geo, h->k, h->d_bad);
+  else if (!q) k_step<S, true, false><<<grid, kBlockX, 0, st>>>(s, d, geo, h->k, h->d_bad);
+  else k_step<S, true, true><<<grid, kBlockX, 0, st>>>(s, d, geo, h->k, h->d_bad);
   return cudaGetLastError();
 }
 
@@ -223,6 +208,18 @@ int ensure_stage(rlb_handle* h) {
 // ----------------------------------------------------------------------------- internal helpers
 namespace rlb {
 void set_handleless_error(const std::string& msg) { g_create_error = msg; }
+
+cudaError_t enqueue_steps(rlb_handle* h, int nsteps, cudaStream_t st) {
+  for (int s = 0; s < nsteps; ++s) {
+    const void* src = h->lat[h->cur];
+    void* dst = h->lat[1 - h->cur];
+    cudaError_t e = h->esize == 8 ? launch_step<double>(h, src, dst, st) : launch_step<float>(h, src, dst, st);
+    if (e != cudaSuccess) return e;
+    h->cur = 1 - h->cur;
+    ++h->steps;
+  }
+  return cudaSuccess;
+}
 
 int validate_taus(double tau_f, double tau_v, double tau_e, double tau_eps, double tau_q, int collision,
                   std::string& why) {
@@ -349,14 +346,8 @@ extern "C" int rlb_set_fields(rlb_handle* h, const double* e, const double* ux, 
 extern "C" int rlb_step(rlb_handle* h, int nsteps) {
   if (!h) return fail(h, RLB_EINVAL, "null handle");
   if (nsteps < 0) return fail(h, RLB_EINVAL, "nsteps must be >= 0");
-  for (int s = 0; s < nsteps; ++s) {
-    const void* src = h->lat[h->cur];
-    void* dst = h->lat[1 - h->cur];
-    cudaError_t e = h->esize == 8 ? launch_step<double>(h, src, dst) : launch_step<float>(h, src, dst);
-    if (e != cudaSuccess) return cuda_fail(h, e, "step kernel launch");
-    h->cur = 1 - h->cur;
-    ++h->steps;
-  }
+  cudaError_t e = rlb::enqueue_steps(h, nsteps, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "step kernel launch");
   return RLB_OK;
 }
 
