@@ -66,6 +66,7 @@ struct StepConst {
   // single-precision copies for the FP32-storage collide
   float omf_f, omf1_f, fA_k_f, fD_k_f, f0_k_f, fA_s_f, fD_s_f, fA_a_f, fD_a_f;
   float omv_f, omv1_f, gA_k_f, gD_k_f, gA_s_f, gD_s_f, gA_a_f, gD_a_f;
+  float ce_f, cp_f, cq_f;
 };
 
 inline StepConst make_step_const(double tau_f, double tau_v, double tau_e, double tau_eps, double tau_q,
@@ -101,6 +102,7 @@ inline StepConst make_step_const(double tau_f, double tau_v, double tau_e, doubl
   k.omv_f = (float)k.omv; k.omv1_f = (float)k.omv1;
   k.gA_k_f = (float)k.gA_k; k.gD_k_f = (float)k.gD_k;
   k.gA_s_f = (float)k.gA_s; k.gD_s_f = (float)k.gD_s; k.gA_a_f = (float)k.gA_a; k.gD_a_f = (float)k.gD_a;
+  k.ce_f = (float)k.ce; k.cp_f = (float)k.cp; k.cq_f = (float)k.cq;
   return k;
 }
 
@@ -148,6 +150,83 @@ __device__ __forceinline__ void node_recover(NodeMacro& m) {
   m.u2 = fma(m.ux, m.ux, fma(m.uy, m.uy, m.uz * m.uz));
   // every comparison is false for NaN, so the negated form also catches NaN
   m.bad = !(A >= 0.0) || !(m.T00 > 0.0) || !(m.P > 0.0) || !(m.u2 < 1.0);
+}
+
+// ---------------------------------------------------------------------------
+// Recovery for the FP32-storage path with the FP64 pipe kept for arithmetic:
+// GB300 retires 2 FP64 instructions per clock per SM, and conversions and
+// compares use the same pipe, so they are done with integer operations here.
+//
+// sqrt and reciprocal: an FP32 hardware seed (about 2^-23) refined by two
+// Newton steps in FP64 (each step squares the relative error), i.e. to the FP64
+// rounding level.
+__device__ __forceinline__ float d2f_trunc_bits(double x) {   // seed only: truncating narrow, normal range
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const int e = (int)((hi >> 20) & 0x7ffu) - 896;
+  const unsigned b = (hi & 0x80000000u) | ((unsigned)(e < 1 ? 1 : (e > 254 ? 254 : e)) << 23) |
+                     ((hi & 0xfffffu) << 3) | (lo >> 29);
+  return __uint_as_float(b);
+}
+__device__ __forceinline__ double sqrt_seeded(double A) {
+  float rf;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(d2f_trunc_bits(A)));
+  const unsigned rb = __float_as_uint(rf);
+  // widen the seed by moving bits (normal range)
+  double y = __hiloint2double((int)((rb & 0x80000000u) | ((((rb >> 23) & 0xffu) + 896u) << 20) | ((rb & 0x7fffffu) >> 3)),
+                              (int)(rb << 29));
+  double e = fma(-A * y, y, 1.0);            // 1 - A y^2
+  y = fma(0.5 * y, e, y);                    // 1/sqrt(A) to ~2^-46
+  const double s = A * y;
+  const double d = fma(-s, s, A);            // A - s^2
+  return fma(0.5 * y, d, s);
+}
+__device__ __forceinline__ double rcp_seeded(double x) {
+  float rf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(d2f_trunc_bits(x)));
+  const unsigned rb = __float_as_uint(rf);
+  double y = __hiloint2double((int)((rb & 0x80000000u) | ((((rb >> 23) & 0xffu) + 896u) << 20) | ((rb & 0x7fffffu) >> 3)),
+                              (int)(rb << 29));
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
+
+// Round-to-nearest-even narrowing of a double to float by moving bits (the
+// result for values inside the normal float range; smaller magnitudes flush to
+// a signed zero, larger saturate to a signed infinity).
+__device__ __forceinline__ float d2f_rn_bits(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu) - 896;
+  unsigned mag = ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const unsigned tail = lo & 0x1fffffffu;
+  mag += (tail > 0x10000000u) | ((tail == 0x10000000u) & (mag & 1u));
+  mag = e < 1 ? 0u : (e > 254 ? 0x7f800000u : mag);
+  return __uint_as_float(sign | mag);
+}
+
+// Integer sign / magnitude tests on the high word of a double.
+__device__ __forceinline__ bool pos_finite_hi(double x) {   // x > 0, finite (hi word of a normal positive)
+  const int hi = __double2hiint(x);
+  return hi > 0 && hi < 0x7ff00000;
+}
+
+__device__ __forceinline__ void node_recover_fast(NodeMacro& m) {
+  const double MM = fma(m.Mx, m.Mx, fma(m.My, m.My, m.Mz * m.Mz));
+  const double A = fma(4.0 * m.T00, m.T00, -3.0 * MM);
+  const double sA = sqrt_seeded(A);
+  m.sigma = fma(2.0, m.T00, sA) * (1.0 / 3.0);
+  const double is = rcp_seeded(m.sigma);
+  m.ux = m.Mx * is;
+  m.uy = m.My * is;
+  m.uz = m.Mz * is;
+  m.P = m.sigma - m.T00;
+  m.u2 = fma(m.ux, m.ux, fma(m.uy, m.uy, m.uz * m.uz));
+  // A > 0, T00 > 0, P > 0 (all finite) and u^2 < 1 (bit patterns of non-negative
+  // doubles order like the values; NaN and Inf fail every test)
+  m.bad = !(pos_finite_hi(A) && pos_finite_hi(m.T00) && pos_finite_hi(m.P) &&
+            (unsigned)__double2hiint(m.u2) < 0x3ff00000u);
 }
 
 // c.u for the 9 pair directions
@@ -240,17 +319,123 @@ __device__ __forceinline__ bool node_collide_f64(double (&f)[19], double (&g)[19
   return m.bad;
 }
 
-// FP32-storage node collide: loads widened to FP64 for the moment sums, the
-// recovery (sqrt, reciprocal) in FP64; equilibria and relaxation in FP32.
+// ----------------------------------------------------------------------------
+// Exact moment sums of FP32 populations (FP32-storage variant).
+//
+// The five conserved sums N0, T00, M_x, M_y, M_z of 19 FP32 values are formed
+// without rounding by error-free extraction (Rump, Ogita & Oishi, "Accurate
+// floating-point summation, part I", SIAM J. Sci. Comput. 31 (2008), ExtractVector):
+// with sigma a power of two at least 2^5 times every |p|, q = fl(fl(sigma + p) - sigma)
+// keeps the leading bits of p on the grid of sigma, r = p - q is exact, and any
+// signed sum of the 19 q is exact in FP32.  Three levels (sigma, 2^-19 sigma,
+// 2^-38 sigma) capture every bit of the inputs when max|p| / min|p| < 2^33 (what
+// is left is below 2^-56 max|p|).  Each sum is returned as three non-overlapping
+// FP32 parts; widening them bit-exactly to FP64 and adding gives the correctly
+// rounded FP64 value of the exact sum -- at least as accurate as FP64 summation,
+// while running on the FP32 and integer pipes instead of GB300's FP64 pipe.
+struct Sums3 {
+  float T00[3], Mx[3], My[3], Mz[3], Sa[3], Sd[3];
+};
+
+__device__ __forceinline__ float pow2_bits(int e) {  // 2^(e - 127), e clamped to the normal range
+  e = e < 1 ? 1 : (e > 254 ? 254 : e);
+  return __uint_as_float((unsigned)e << 23);
+}
+
+// Largest biased exponent of |p| over the 19 values (255 if any is Inf or NaN).
+__device__ __forceinline__ int max_exp19(const float (&p)[19]) {
+  unsigned m = __float_as_uint(p[0]) & 0x7fffffffu;
+#pragma unroll
+  for (int a = 1; a < 19; ++a) m = max(m, __float_as_uint(p[a]) & 0x7fffffffu);
+  return (int)(m >> 23);
+}
+
+// Widen an FP32 value to FP64 by moving its bits (exact; no FP64-pipe conversion).
+__device__ __forceinline__ double f2d_bits(float x) {
+  const unsigned b = __float_as_uint(x);
+  const unsigned ex = (b >> 23) & 0xffu;
+  // zero and subnormal parts (below 2^-126) flush to a signed zero
+  const unsigned hi = ex == 0u ? (b & 0x80000000u) : ((b & 0x80000000u) | ((ex + 896u) << 20) | ((b & 0x7fffffu) >> 3));
+  return __hiloint2double((int)hi, ex == 0u ? 0 : (int)(b << 29));
+}
+
+__device__ __forceinline__ double sum3_to_f64(const float (&v)[3]) {
+  return (f2d_bits(v[0]) + f2d_bits(v[1])) + f2d_bits(v[2]);
+}
+
+// Exact level sums of g: T00, M, and the axis / diagonal class sums.
+__device__ __forceinline__ bool exact_sums_g(const float (&g)[19], Sums3& S) {
+  const int E = max_exp19(g);
+  const float sg[3] = {pow2_bits(E + 6), pow2_bits(E - 13), pow2_bits(E - 32)};
+  float r[19];
+#pragma unroll
+  for (int a = 0; a < 19; ++a) r[a] = g[a];
+#pragma unroll
+  for (int L = 0; L < 3; ++L) {
+    float q[19];
+#pragma unroll
+    for (int a = 0; a < 19; ++a) {
+      const float t = sg[L] + r[a];
+      q[a] = t - sg[L];
+      r[a] = r[a] - q[a];
+    }
+    float d[9];
+#pragma unroll
+    for (int pp = 0; pp < 9; ++pp) d[pp] = q[2 * pp + 1] - q[2 * pp + 2];
+    S.Sa[L] = ((q[1] + q[2]) + (q[3] + q[4])) + (q[5] + q[6]);
+    S.Sd[L] = (((q[7] + q[8]) + (q[9] + q[10])) + ((q[11] + q[12]) + (q[13] + q[14]))) +
+              ((q[15] + q[16]) + (q[17] + q[18]));
+    S.T00[L] = (q[0] + S.Sa[L]) + S.Sd[L];
+    S.Mx[L] = ((d[0] + d[3]) + (d[4] + d[5])) + d[6];
+    S.My[L] = ((d[1] + d[3]) - (d[4] - d[7])) + d[8];
+    S.Mz[L] = ((d[2] + d[5]) - (d[6] - d[7])) - d[8];
+  }
+  return E == 255;
+}
+
+__device__ __forceinline__ bool exact_sum_f(const float (&f)[19], float (&N0)[3]) {
+  const int E = max_exp19(f);
+  const float sg[3] = {pow2_bits(E + 6), pow2_bits(E - 13), pow2_bits(E - 32)};
+  float r[19];
+#pragma unroll
+  for (int a = 0; a < 19; ++a) r[a] = f[a];
+#pragma unroll
+  for (int L = 0; L < 3; ++L) {
+    float q[19];
+#pragma unroll
+    for (int a = 0; a < 19; ++a) {
+      const float t = sg[L] + r[a];
+      q[a] = t - sg[L];
+      r[a] = r[a] - q[a];
+    }
+    N0[L] = ((((q[0] + q[1]) + (q[2] + q[3])) + ((q[4] + q[5]) + (q[6] + q[7]))) +
+             (((q[8] + q[9]) + (q[10] + q[11])) + ((q[12] + q[13]) + (q[14] + q[15])))) +
+            ((q[16] + q[17]) + q[18]);
+  }
+  return E == 255;
+}
+
+// FP32-storage node collide: the conserved sums exact (above) and delivered in
+// FP64, the recovery (sqrt, reciprocal) in FP64; equilibria, MRT projection and
+// relaxation in FP32 with one rounding on store.
 template <bool MRT, bool QSEP>
 __device__ __forceinline__ bool node_collide_f32s(float (&f)[19], float (&g)[19], const StepConst& k) {
-  double sp[9], dp[9], Sa, Sd;
+  Sums3 S;
+  float N0p[3];
+  bool nonfinite = exact_sums_g(g, S);
+  nonfinite |= exact_sum_f(f, N0p);
   NodeMacro m;
-  node_moments<float>(f, g, sp, dp, Sa, Sd, m);
-  node_recover(m);
+  m.T00 = sum3_to_f64(S.T00);
+  m.Mx = sum3_to_f64(S.Mx);
+  m.My = sum3_to_f64(S.My);
+  m.Mz = sum3_to_f64(S.Mz);
+  m.N0 = sum3_to_f64(N0p);
+  node_recover_fast(m);
+  m.bad |= nonfinite;
 
-  const float ux = (float)m.ux, uy = (float)m.uy, uz = (float)m.uz;
-  const float u2 = (float)m.u2, N0 = (float)m.N0, sg = (float)m.sigma, P = (float)m.P;
+  const float ux = d2f_rn_bits(m.ux), uy = d2f_rn_bits(m.uy), uz = d2f_rn_bits(m.uz);
+  const float N0 = d2f_rn_bits(m.N0), sg = d2f_rn_bits(m.sigma), P = d2f_rn_bits(m.P);
+  const float u2 = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
   float cu[9];
   pair_cu<float>(ux, uy, uz, cu);
   {
@@ -269,12 +454,12 @@ __device__ __forceinline__ bool node_collide_f32s(float (&f)[19], float (&g)[19]
     }
   }
   {
+    // the two per-node equilibrium constants cancel (sigma ~ 4P): formed in FP64
     const double su2d = m.sigma * m.u2;
-    const float su2 = (float)su2d;
-    const float P3 = 3.0f * P;
-    const float kg = fmaf(-1.5f, su2, P3);
-    const double geq0d = fma(-0.5, su2d, m.sigma - 3.0 * m.P);
-    const float geq0 = (float)geq0d;
+    const double P3d = 3.0 * m.P;
+    const float su2 = d2f_rn_bits(su2d);
+    const float kg = d2f_rn_bits(fma(-1.5, su2d, P3d));
+    const float geq0 = d2f_rn_bits(fma(-0.5, su2d, m.sigma - P3d));
     float KA = k.gA_k_f * kg, KD = k.gD_k_f * kg;
     const float SA = k.gA_s_f * sg, SD = k.gD_s_f * sg;
     const float AA = k.gA_a_f * sg, AD = k.gD_a_f * sg;
@@ -283,23 +468,29 @@ __device__ __forceinline__ bool node_collide_f32s(float (&f)[19], float (&g)[19]
 #pragma unroll
     for (int p = 0; p < 9; ++p) dq[p] = 0.0f;
     if (MRT) {
-      const double n0 = (double)g[0] - geq0d;
-      const double nA = Sa - m.P;
-      const double nD = fma(-0.5, su2d, Sd - m.P);
-      const double ne = fma(8.0, nD, fma(-11.0, nA, -30.0 * n0));
-      const double np = fma(-4.0, nA, fma(12.0, n0, nD));
-      const float ae = (float)(k.ce * ne), ap = (float)(k.cp * np);
+      // non-equilibrium class sums in FP32 (their rounding is far below the FP32 storage rounding)
+      const float Sa = (S.Sa[0] + S.Sa[1]) + S.Sa[2];
+      const float Sd = (S.Sd[0] + S.Sd[1]) + S.Sd[2];
+      const float n0 = g[0] - geq0;
+      const float nA = Sa - P;
+      const float nD = fmaf(-0.5f, su2, Sd - P);
+      const float ne = fmaf(8.0f, nD, fmaf(-11.0f, nA, -30.0f * n0));
+      const float np = fmaf(-4.0f, nA, fmaf(12.0f, n0, nD));
+      const float ae = k.ce_f * ne, ap = k.cp_f * np;
       g0n = g0n + fmaf(30.0f, ae, -12.0f * ap);
       KA = KA + fmaf(11.0f, ae, 4.0f * ap);
       KD = KD - fmaf(8.0f, ae, ap);
       if (QSEP) {
-        const double qeq = -2.0 / 3.0;
-        const double qx = fma(-4.0, dp[0], ((dp[3] + dp[4]) + dp[5]) + dp[6]);
-        const double qy = fma(-4.0, dp[1], ((dp[3] - dp[4]) + dp[7]) + dp[8]);
-        const double qz = fma(-4.0, dp[2], ((dp[5] - dp[6]) + dp[7]) - dp[8]);
-        const float aqx = (float)(k.cq * fma(-qeq, m.Mx, qx));
-        const float aqy = (float)(k.cq * fma(-qeq, m.My, qy));
-        const float aqz = (float)(k.cq * fma(-qeq, m.Mz, qz));
+        const float qeq = -2.0f / 3.0f;
+        const float d0 = g[1] - g[2], d1 = g[3] - g[4], d2 = g[5] - g[6], d3 = g[7] - g[8], d4 = g[9] - g[10];
+        const float d5 = g[11] - g[12], d6 = g[13] - g[14], d7 = g[15] - g[16], d8 = g[17] - g[18];
+        const float qx = fmaf(-4.0f, d0, ((d3 + d4) + d5) + d6);
+        const float qy = fmaf(-4.0f, d1, ((d3 - d4) + d7) + d8);
+        const float qz = fmaf(-4.0f, d2, ((d5 - d6) + d7) - d8);
+        const float cq = k.cq_f;
+        const float aqx = cq * fmaf(-qeq, d2f_rn_bits(m.Mx), qx);
+        const float aqy = cq * fmaf(-qeq, d2f_rn_bits(m.My), qy);
+        const float aqz = cq * fmaf(-qeq, d2f_rn_bits(m.Mz), qz);
         dq[0] = 4.0f * aqx; dq[1] = 4.0f * aqy; dq[2] = 4.0f * aqz;
         dq[3] = -(aqx + aqy); dq[4] = -(aqx - aqy);
         dq[5] = -(aqx + aqz); dq[6] = -(aqx - aqz);
