@@ -216,7 +216,7 @@ template <bool MRT>
 __global__ void __launch_bounds__(kThreads) k_adj_collide(const double* __restrict__ g, const double* __restrict__ lam,
                                                          double* __restrict__ mu, double* __restrict__ tb, AGeo geo,
                                                          StepConst k) {
-  const unsigned long long i = blockIdx.x * (unsigned long long)kThreads + threadIdx.x;
+  const unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
   if (i >= geo.n) return;
   const int x = (int)(i % geo.nx), y = (int)((i / geo.nx) % geo.ny), z = (int)(i / ((unsigned long long)geo.nx * geo.ny));
   double h[19], lo[19], hb[19];
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_collide(const double* __restri
 
 __global__ void __launch_bounds__(kThreads) k_adj_stream(const double* __restrict__ mu, double* __restrict__ lam,
                                                         AGeo geo) {
-  const unsigned long long i = blockIdx.x * (unsigned long long)kThreads + threadIdx.x;
+  const unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
   if (i >= geo.n) return;
   const int x = (int)(i % geo.nx), y = (int)((i / geo.nx) % geo.ny), z = (int)(i / ((unsigned long long)geo.nx * geo.ny));
 #pragma unroll
@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_loss(const double* __restrict_
                                                       const double* __restrict__ tuz, double wP, double wu,
                                                       double* __restrict__ lam, double* __restrict__ lossn,
                                                       unsigned long long n) {
-  const unsigned long long i = blockIdx.x * (unsigned long long)kThreads + threadIdx.x;
+  const unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
   if (i >= n) return;
   double h[19], hb[19];
 #pragma unroll
@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_loss(const double* __restrict_
 // dJ/de0 of an equilibrium initial state: g^0 is linear in e0, so sum_a lambda_a g0_a / e0.
 __global__ void __launch_bounds__(kThreads) k_adj_e0(const double* __restrict__ g0, const double* __restrict__ lam,
                                                     double* __restrict__ de0, unsigned long long n) {
-  const unsigned long long i = blockIdx.x * (unsigned long long)kThreads + threadIdx.x;
+  const unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
   if (i >= n) return;
   double h[19];
   double acc = 0.0;
@@ -322,21 +322,96 @@ int afail(rlb_handle* h, int code, const std::string& m) {
   return code;
 }
 
-struct DevBufs {
-  std::vector<void*> ptrs;
-  ~DevBufs() {
-    for (void* p : ptrs) cudaFree(p);
-  }
-  bool get(void** p, size_t bytes) {
-    if (cudaMalloc(p, bytes) != cudaSuccess) {
-      cudaGetLastError();
-      *p = nullptr;
-      return false;
-    }
-    ptrs.push_back(*p);
-    return true;
-  }
+// Buffers and the captured CUDA graph of one (nsteps, checkpoint interval) shape,
+// kept on the handle so repeated gradients replay instead of re-launching ~4 T
+// kernels one by one.
+struct AdjPlan {
+  int nsteps = -1, K = 0, nseg = 0, start_cur = 0, threads = 128;
+  double wP = 0.0, wu = 0.0;                  // misfit weights baked into the graph
+  std::vector<void*> ckpt, seg, owned;
+  double *lam = nullptr, *mu = nullptr, *tb = nullptr, *lossn = nullptr, *sums = nullptr, *dde0 = nullptr;
+  double* tgt = nullptr;
+  void* g0copy = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
 };
+
+void free_plan(void* p) {
+  AdjPlan* a = (AdjPlan*)p;
+  if (!a) return;
+  if (a->exec) cudaGraphExecDestroy(a->exec);
+  if (a->graph) cudaGraphDestroy(a->graph);
+  if (a->cap) cudaStreamDestroy(a->cap);
+  for (void* q : a->owned) cudaFree(q);
+  delete a;
+}
+
+bool plan_alloc(AdjPlan* a, void** p, size_t bytes) {
+  if (cudaMalloc(p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return false;
+  }
+  a->owned.push_back(*p);
+  return true;
+}
+
+// Enqueue the whole gradient computation on stream st (captured into the plan's graph).
+cudaError_t enqueue_adjoint(rlb_handle* h, AdjPlan* a, double wP, double wu, bool mrt) {
+  const unsigned long long N = h->nodes;
+  const size_t state_bytes = 38 * N * sizeof(double);
+  const int T = a->nsteps, K = a->K, th = a->threads;
+  const unsigned grid = (unsigned)((N + th - 1) / th);
+  cudaStream_t st = a->cap;
+  AGeo geo{h->cfg.nx, h->cfg.ny, h->cfg.nz, h->cfg.bc[0] == RLB_ZERO_GRADIENT, h->cfg.bc[1] == RLB_ZERO_GRADIENT,
+           h->cfg.bc[2] == RLB_ZERO_GRADIENT, N};
+  const double* tP = a->tgt;
+  cudaError_t e;
+#define ENQ(call) do { e = (call); if (e != cudaSuccess) return e; } while (0)
+  // forward with checkpoints
+  ENQ(cudaMemcpyAsync(a->g0copy, h->lat[h->cur], state_bytes, cudaMemcpyDeviceToDevice, st));
+  for (int t = 0; t < T; ++t) {
+    if (t % K == 0) ENQ(cudaMemcpyAsync(a->ckpt[t / K], h->lat[h->cur], state_bytes, cudaMemcpyDeviceToDevice, st));
+    ENQ(enqueue_steps(h, 1, st));
+  }
+  // misfit and lambda^T
+  const double* gT = (const double*)h->lat[h->cur] + 19 * N;
+  k_adj_loss<<<grid, th, 0, st>>>(gT, tP, tP + N, tP + 2 * N, tP + 3 * N, wP, wu, a->lam, a->lossn, N);
+  ENQ(cudaGetLastError());
+  ENQ(cudaMemsetAsync(a->tb, 0, 3 * N * sizeof(double), st));
+  // reverse sweep, segment by segment, recomputing each from its checkpoint
+  void* saved[2] = {h->lat[0], h->lat[1]};
+  const int saved_cur = h->cur;
+  for (int s = a->nseg - 1; s >= 0; --s) {
+    const int t0 = s * K, t1 = std::min(T, t0 + K);
+    ENQ(cudaMemcpyAsync(a->seg[0], a->ckpt[s], state_bytes, cudaMemcpyDeviceToDevice, st));
+    for (int j = 0; j + 1 < t1 - t0; ++j) {   // seg[j] holds g^{t0 + j}
+      h->lat[0] = a->seg[j];
+      h->lat[1] = a->seg[j + 1];
+      h->cur = 0;
+      e = enqueue_steps(h, 1, st);
+      if (e != cudaSuccess) break;
+    }
+    h->lat[0] = saved[0];
+    h->lat[1] = saved[1];
+    h->cur = saved_cur;
+    if (e != cudaSuccess) return e;
+    for (int t = t1 - 1; t >= t0; --t) {
+      const double* gt = (const double*)a->seg[t - t0] + 19 * N;
+      if (mrt) k_adj_collide<true><<<grid, th, 0, st>>>(gt, a->lam, a->mu, a->tb, geo, h->k);
+      else k_adj_collide<false><<<grid, th, 0, st>>>(gt, a->lam, a->mu, a->tb, geo, h->k);
+      k_adj_stream<<<grid, th, 0, st>>>(a->mu, a->lam, geo);
+    }
+  }
+  ENQ(cudaGetLastError());
+  k_adj_e0<<<grid, th, 0, st>>>((const double*)a->g0copy + 19 * N, a->lam, a->dde0, N);
+  k_rowsum<<<3, 256, 0, st>>>(a->tb, N, a->sums);
+  k_rowsum<<<1, 256, 0, st>>>(a->lossn, N, a->sums + 3);
+  ENQ(cudaGetLastError());
+#undef ENQ
+  return cudaSuccess;
+}
 
 }  // namespace
 
@@ -344,7 +419,7 @@ extern "C" int rlb_adjoint(rlb_handle* h, int nsteps, int checkpoint_every, cons
                            const double* target_ux, const double* target_uy, const double* target_uz, double w_P,
                            double w_u, int where, double* loss, double* dtau, double* de0) {
   if (!h) return RLB_EINVAL;
-  if (nsteps < 0) return afail(h, RLB_EINVAL, "nsteps must be >= 0");
+  if (nsteps < 1) return afail(h, RLB_EINVAL, "nsteps must be >= 1");
   if (!target_P || !target_ux || !target_uy || !target_uz || !loss || !dtau)
     return afail(h, RLB_EINVAL, "null argument");
   if (where != RLB_HOST && where != RLB_DEVICE) return afail(h, RLB_EINVAL, "where must be RLB_HOST or RLB_DEVICE");
@@ -355,23 +430,7 @@ extern "C" int rlb_adjoint(rlb_handle* h, int nsteps, int checkpoint_every, cons
   const unsigned long long N = h->nodes;
   const size_t state_bytes = 38 * N * sizeof(double), gbytes = 19 * N * sizeof(double);
   const int K = checkpoint_every > 0 ? checkpoint_every : std::max(1, (int)std::ceil(std::sqrt((double)nsteps)));
-  const int nseg = nsteps > 0 ? (nsteps + K - 1) / K : 0;
   cudaStream_t st = h->stream;
-
-  DevBufs mem;
-  std::vector<void*> ckpt(nseg, nullptr), seg(K + 1, nullptr);
-  double *lam = nullptr, *mu = nullptr, *tb = nullptr, *lossn = nullptr, *sums = nullptr, *tgt = nullptr;
-  double* dde0 = nullptr;
-  bool ok = true;
-  for (int s = 0; s < nseg && ok; ++s) ok = mem.get(&ckpt[s], state_bytes);
-  for (int j = 0; j <= K && ok && nsteps > 0; ++j) ok = mem.get(&seg[j], state_bytes);
-  ok = ok && mem.get((void**)&lam, gbytes) && mem.get((void**)&mu, gbytes) &&
-       mem.get((void**)&tb, 3 * N * sizeof(double)) && mem.get((void**)&lossn, N * sizeof(double)) &&
-       mem.get((void**)&sums, 8 * sizeof(double)) && mem.get((void**)&dde0, N * sizeof(double));
-  void* g0copy = nullptr;
-  ok = ok && mem.get(&g0copy, state_bytes);
-  if (ok && where == RLB_HOST) ok = mem.get((void**)&tgt, 4 * N * sizeof(double));
-  if (!ok) return afail(h, RLB_ENOMEM, "cannot allocate adjoint checkpoints and buffers");
 
 #define ACUDA(call)                                                                       \
   do {                                                                                    \
@@ -379,26 +438,79 @@ extern "C" int rlb_adjoint(rlb_handle* h, int nsteps, int checkpoint_every, cons
     if (e_ != cudaSuccess) return afail(h, RLB_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
-  const double* tP = target_P;
-  const double *tx = target_ux, *ty = target_uy, *tz = target_uz;
-  if (where == RLB_HOST) {
+  // ---- plan (buffers + graph) for this shape
+  AdjPlan* a = (AdjPlan*)h->adj_plan;
+  if (a && (a->nsteps != nsteps || a->K != std::min(K, nsteps))) {
+    ACUDA(cudaStreamSynchronize(st));
+    free_plan(a);
+    h->adj_plan = nullptr;
+    a = nullptr;
+  }
+  if (!a) {
+    a = new AdjPlan();
+    a->nsteps = nsteps;
+    a->K = std::min(K, nsteps);
+    a->nseg = (nsteps + a->K - 1) / a->K;
+    a->threads = N <= 152ull * 128ull * 2ull ? 32 : 128;
+    a->ckpt.assign(a->nseg, nullptr);
+    a->seg.assign(a->K + 1, nullptr);
+    bool ok = true;
+    for (int s = 0; s < a->nseg && ok; ++s) ok = plan_alloc(a, &a->ckpt[s], state_bytes);
+    for (int j = 0; j <= a->K && ok; ++j) ok = plan_alloc(a, &a->seg[j], state_bytes);
+    ok = ok && plan_alloc(a, (void**)&a->lam, gbytes) && plan_alloc(a, (void**)&a->mu, gbytes) &&
+         plan_alloc(a, (void**)&a->tb, 3 * N * sizeof(double)) && plan_alloc(a, (void**)&a->lossn, N * sizeof(double)) &&
+         plan_alloc(a, (void**)&a->sums, 8 * sizeof(double)) && plan_alloc(a, (void**)&a->dde0, N * sizeof(double)) &&
+         plan_alloc(a, (void**)&a->tgt, 4 * N * sizeof(double)) && plan_alloc(a, &a->g0copy, state_bytes);
+    if (!ok || cudaStreamCreateWithFlags(&a->cap, cudaStreamNonBlocking) != cudaSuccess) {
+      free_plan(a);
+      return afail(h, RLB_ENOMEM, "cannot allocate adjoint checkpoints and buffers");
+    }
+    a->start_cur = h->cur;
+    h->adj_plan = a;
+    h->adj_free = free_plan;
+  }
+  // the graph's lattice pointers assume the state starts in lat[start_cur]
+  if (h->cur != a->start_cur) {
+    ACUDA(cudaMemcpyAsync(h->lat[a->start_cur], h->lat[h->cur], state_bytes, cudaMemcpyDeviceToDevice, st));
+    h->cur = a->start_cur;
+  }
+  // targets into the plan's buffer (outside the graph)
+  {
     const double* src[4] = {target_P, target_ux, target_uy, target_uz};
     for (int c = 0; c < 4; ++c)
-      ACUDA(cudaMemcpyAsync(tgt + c * N, src[c], N * sizeof(double), cudaMemcpyHostToDevice, st));
-    tP = tgt; tx = tgt + N; ty = tgt + 2 * N; tz = tgt + 3 * N;
+      ACUDA(cudaMemcpyAsync(a->tgt + c * N, src[c], N * sizeof(double),
+                            where == RLB_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
   }
-  AGeo geo{h->cfg.nx, h->cfg.ny, h->cfg.nz, h->cfg.bc[0] == RLB_ZERO_GRADIENT, h->cfg.bc[1] == RLB_ZERO_GRADIENT,
-           h->cfg.bc[2] == RLB_ZERO_GRADIENT, N};
-  const unsigned grid = (unsigned)((N + kThreads - 1) / kThreads);
-
-  // ---- forward with checkpoints
-  ACUDA(cudaMemcpyAsync(g0copy, h->lat[h->cur], state_bytes, cudaMemcpyDeviceToDevice, st));
-  for (int t = 0; t < nsteps; ++t) {
-    if (t % K == 0) ACUDA(cudaMemcpyAsync(ckpt[t / K], h->lat[h->cur], state_bytes, cudaMemcpyDeviceToDevice, st));
-    ACUDA(enqueue_steps(h, 1, st));
+  // capture once per plan (the misfit weights are kernel arguments: recapture if they change)
+  if (!a->exec || a->wP != w_P || a->wu != w_u) {
+    if (a->exec) { cudaGraphExecDestroy(a->exec); a->exec = nullptr; }
+    if (a->graph) { cudaGraphDestroy(a->graph); a->graph = nullptr; }
+    const long long steps0 = h->steps;
+    ACUDA(cudaStreamBeginCapture(a->cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t ce = enqueue_adjoint(h, a, w_P, w_u, mrt);
+    cudaGraph_t g = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(a->cap, &g);
+    h->cur = a->start_cur;   // nothing ran yet
+    h->steps = steps0;
+    if (ce != cudaSuccess || ee != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return afail(h, RLB_ECUDA, std::string("adjoint graph capture: ") + cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+    }
+    a->graph = g;
+    ACUDA(cudaGraphInstantiate(&a->exec, a->graph, 0));
+    a->wP = w_P;
+    a->wu = w_u;
   }
+  ACUDA(cudaGraphLaunch(a->exec, st));
+  double hs[4];
+  ACUDA(cudaMemcpyAsync(hs, a->sums, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (de0)
+    ACUDA(cudaMemcpyAsync(de0, a->dde0, N * sizeof(double),
+                          where == RLB_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+  ACUDA(cudaStreamSynchronize(st));
+  h->cur = a->start_cur ^ (nsteps & 1);
+  h->steps += nsteps;
   {
-    ACUDA(cudaStreamSynchronize(st));
     unsigned long long bad = ~0ull;
     ACUDA(cudaMemcpy(&bad, h->d_bad, sizeof bad, cudaMemcpyDeviceToHost));
     if (bad != ~0ull) {
@@ -409,55 +521,6 @@ extern "C" int rlb_adjoint(rlb_handle* h, int nsteps, int checkpoint_every, cons
       return afail(h, RLB_ENONPHYS, buf);
     }
   }
-  void* final_state = h->lat[h->cur];
-  const long long steps_before = h->steps;
-  // ---- loss and lambda^T
-  const double* gT = (const double*)final_state + 19 * N;
-  k_adj_loss<<<grid, kThreads, 0, st>>>(gT, tP, tx, ty, tz, w_P, w_u, lam, lossn, N);
-  ACUDA(cudaGetLastError());
-  ACUDA(cudaMemsetAsync(tb, 0, 3 * N * sizeof(double), st));
-
-  // ---- backward over segments, recomputing each segment from its checkpoint
-  void* saved_lat[2] = {h->lat[0], h->lat[1]};
-  const int saved_cur = h->cur;
-  for (int s = nseg - 1; s >= 0; --s) {
-    const int t0 = s * K, t1 = std::min(nsteps, t0 + K);
-    ACUDA(cudaMemcpyAsync(seg[0], ckpt[s], state_bytes, cudaMemcpyDeviceToDevice, st));
-    for (int j = 0; j + 1 < t1 - t0; ++j) {   // seg[j] holds g^{t0 + j}
-      h->lat[0] = seg[j];
-      h->lat[1] = seg[j + 1];
-      h->cur = 0;
-      cudaError_t e = enqueue_steps(h, 1, st);
-      if (e != cudaSuccess) {
-        h->lat[0] = saved_lat[0]; h->lat[1] = saved_lat[1]; h->cur = saved_cur;
-        return afail(h, RLB_ECUDA, std::string("recompute: ") + cudaGetErrorString(e));
-      }
-    }
-    for (int t = t1 - 1; t >= t0; --t) {
-      const double* gt = (const double*)seg[t - t0] + 19 * N;
-      if (mrt) k_adj_collide<true><<<grid, kThreads, 0, st>>>(gt, lam, mu, tb, geo, h->k);
-      else k_adj_collide<false><<<grid, kThreads, 0, st>>>(gt, lam, mu, tb, geo, h->k);
-      k_adj_stream<<<grid, kThreads, 0, st>>>(mu, lam, geo);
-    }
-  }
-  h->lat[0] = saved_lat[0];
-  h->lat[1] = saved_lat[1];
-  h->cur = saved_cur;
-  h->steps = steps_before;
-  ACUDA(cudaGetLastError());
-  if (h->lat[h->cur] != final_state) return afail(h, RLB_ECUDA, "internal: lattice bookkeeping");
-
-  // ---- dJ/de0, sums
-  k_adj_e0<<<grid, kThreads, 0, st>>>((const double*)g0copy + 19 * N, lam, dde0, N);
-  k_rowsum<<<3, 256, 0, st>>>(tb, N, sums);
-  k_rowsum<<<1, 256, 0, st>>>(lossn, N, sums + 3);
-  ACUDA(cudaGetLastError());
-  double hs[4];
-  ACUDA(cudaMemcpyAsync(hs, sums, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
-  if (de0)
-    ACUDA(cudaMemcpyAsync(de0, dde0, N * sizeof(double),
-                          where == RLB_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
-  ACUDA(cudaStreamSynchronize(st));
   // omega = 1 / tau  =>  dJ/dtau = -omega^2 dJ/domega
   const double wv = 1.0 / h->cfg.tau_v;
   *loss = hs[3];

@@ -23,6 +23,8 @@ struct rlb_handle {
   rlb::StepConst k{};
   long long steps = 0;
   std::string err;
+  void* adj_plan = nullptr;                       // cached adjoint buffers and graph (rlb_adjoint)
+  void (*adj_free)(void*) = nullptr;              // its destructor
 };
 
 

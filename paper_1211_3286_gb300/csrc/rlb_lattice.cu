@@ -81,7 +81,7 @@ __device__ __forceinline__ void pull19(const S* __restrict__ base, unsigned long
 template <typename S, bool MRT, bool QSEP>
 __global__ void __launch_bounds__(kBlockX) k_step(const S* __restrict__ src, S* __restrict__ dst, Geo geo,
                                                   StepConst k, unsigned long long* __restrict__ bad) {
-  const int x = blockIdx.x * kBlockX + threadIdx.x;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= geo.nx) return;
   const int y = blockIdx.y, z = blockIdx.z;
   // source coordinates for offsets c = +1, 0, -1 (index 0, 1, 2 = 1 - c)
@@ -166,13 +166,17 @@ bool qsep(const rlb_config& c) { return c.collision == RLB_MRT && c.tau_q > 0 &&
 template <typename S>
 cudaError_t launch_step(rlb_handle* h, const void* src, void* dst, cudaStream_t st) {
   const Geo geo = make_geo(h);
-  dim3 grid((geo.nx + kBlockX - 1) / kBlockX, geo.ny, geo.nz);
+  // small lattices (a 1600-node tube) spread over more SMs with one warp per block:
+  // the FP64 pipe of an SM serves 2 lanes per clock, so fewer warps per SM means
+  // shorter steps when the lattice cannot fill the GPU anyway
+  const int bx = h->nodes <= 152ull * 128ull * 2ull ? 32 : kBlockX;
+  dim3 grid((geo.nx + bx - 1) / bx, geo.ny, geo.nz);
   const bool mrt = h->cfg.collision == RLB_MRT, q = qsep(h->cfg);
   const S* s = (const S*)src;
   S* d = (S*)dst;
-  if (!mrt) k_step<S, false, false><<<grid, kBlockX, 0, st>>>(s, d, geo, h->k, h->d_bad);
-  else if (!q) k_step<S, true, false><<<grid, kBlockX, 0, st>>>(s, d, geo, h->k, h->d_bad);
-  else k_step<S, true, true><<<grid, kBlockX, 0, st>>>(s, d, geo, h->k, h->d_bad);
+  if (!mrt) k_step<S, false, false><<<grid, bx, 0, st>>>(s, d, geo, h->k, h->d_bad);
+  else if (!q) k_step<S, true, false><<<grid, bx, 0, st>>>(s, d, geo, h->k, h->d_bad);
+  else k_step<S, true, true><<<grid, bx, 0, st>>>(s, d, geo, h->k, h->d_bad);
   return cudaGetLastError();
 }
 
@@ -285,6 +289,7 @@ extern "C" int rlb_create(const rlb_config* cfg, rlb_handle** out) {
 extern "C" void rlb_destroy(rlb_handle* h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
+  if (h->adj_plan && h->adj_free) h->adj_free(h->adj_plan);
   for (int i = 0; i < 2; ++i)
     if (h->lat[i]) cudaFree(h->lat[i]);
   if (h->d_bad) cudaFree(h->d_bad);

@@ -245,7 +245,7 @@ __device__ __forceinline__ bool node_collide_f64(double (&f)[19], double (&g)[19
   double sp[9], dp[9], Sa, Sd;
   NodeMacro m;
   node_moments<double>(f, g, sp, dp, Sa, Sd, m);
-  node_recover(m);
+  node_recover_fast(m);
 
   double cu[9];
   pair_cu<double>(m.ux, m.uy, m.uz, cu);
