@@ -49,19 +49,27 @@ WORKLOADS = {
                     desc="adjoint: quasi-1D D3Q19 shock tube of 1600 nodes, FP64 MRT (0.9, 0.55, 0.8), 4000 steps "
                          "with sqrt(T) checkpoints; gradient of the P/u profile misfit w.r.t. tau_v, tau_e, "
                          "tau_eps and the 1600-value initial e field (forward + recompute + reverse)"),
+    "tubes_small": dict(N=None, precision="fp32", dtype="f32-storage/f64-recovery", bytes_per_update=304,
+                        desc="small profiling case of the tau sweep: 128 tubes of the same length / tau "
+                             "distribution, FP32 storage"),
     "box512_fp32": dict(N=512, precision="fp32", dtype="f32-storage/f64-recovery", bytes_per_update=304,
                         desc="3-D MRT periodic box, D3Q19, 512^3 nodes, FP32 population storage with FP64 sums "
                              "and recovery, same fields and taus, 200 steps"),
 }
 TAUS = dict(tau_f=0.9, tau_v=0.9, tau_e=0.55, tau_eps=0.8)
 
-# FP64 flops of one FP32-storage node update: moment sums 57 + recovery 23.
-FLOPS_PER_UPDATE_F32S_FP64PART = 80
+# FP64 operations of one FP32-storage node update (the sums are exact on the FP32
+# and integer pipes): recovery on the unscaled integer sums 17 + 5 conversions of
+# the integer sums + equilibrium constants 5.
+FP64_OPS_PER_UPDATE_F32S = 27
 
 # FP64 flops (FMA = 2, sqrt and division = 1) of one FP64 MRT node update,
 # counted from the per-node arithmetic of the step kernel: moments 57,
 # recovery 23, f relaxation 102 (+6 pair velocities), g relaxation 97, MRT 27.
 FLOPS_PER_UPDATE_F64 = 312
+# The same per-node arithmetic counted as FP64 operations (FMA = 1): moments 57,
+# recovery 17, pair velocities 6, f relaxation 73, g relaxation 87 (MRT 20 of it).
+FP64_OPS_PER_UPDATE = 240
 
 
 def _dist():
@@ -72,6 +80,21 @@ def _dist():
             dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
         return dist, dist.get_rank(), ws
     return None, 0, 1
+
+
+def reduce_max(value: float, dist) -> float:
+    """Max of a per-rank float over all ranks (the job's elapsed time)."""
+    if dist is None:
+        return value
+    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world_size: int, seconds: float) -> float:
+    """Whole-job throughput: units of all replicas over the slowest rank's time (MLUPS for node updates)."""
+    return units_per_rank * world_size / seconds / 1e6
 
 
 def _peaks():
@@ -143,7 +166,7 @@ class ClockSampler:
 def cpu_baseline(seconds_budget=15.0):
     """The oracle (plain FP64, torch CPU ops) on a bounded sample of the workload:
     a 48^3 box of the same generator and relaxation times, as many steps as fit the
-    budget (at least 2).  Returns MLUPS and what was run."""
+    budget (at least 1).  Returns MLUPS and what was run."""
     import oracle.rlb_oracle as O
     from paper_1211_3286_gb300 import inputs as I
     n = 48
@@ -152,7 +175,7 @@ def cpu_baseline(seconds_budget=15.0):
     f, g = O.init_populations(e, torch.stack([ux, uy, uz]), nn)
     t0 = time.perf_counter()
     steps = 0
-    while steps < 2 or (time.perf_counter() - t0 < seconds_budget and steps < 200):
+    while steps < 1 or (time.perf_counter() - t0 < seconds_budget and steps < 200):
         f, g = O.step(f, g, prm)
         steps += 1
     dt = time.perf_counter() - t0
@@ -166,8 +189,7 @@ def run_reference(args):
     if rank != 0:
         return
     wl = WORKLOADS[args.workload]
-    budget = max(10.0, 2.0 * args.steps)
-    cb = cpu_baseline(min(budget, 60.0))
+    cb = cpu_baseline(args.ref_seconds)
     line = {"impl": "reference", "metric": "MLUPS", "value": cb["value"], "unit": "MLUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -181,8 +203,8 @@ def run_tubes(args, dist, rank, ws, local):
     import numpy as np
     from paper_1211_3286_gb300 import inputs as I
     from paper_1211_3286_gb300.batch import TubeBatch
-    wl = WORKLOADS["tubes"]
-    lengths, taus = I.tube_sweep(1024)
+    wl = WORKLOADS[args.workload]
+    lengths, taus = I.tube_sweep(128 if args.workload == "tubes_small" else 1024)
     nodes = int(lengths.sum())
     parts = [I.shock_tube(int(L)) for L in lengths]
     fields = [torch.from_numpy(np.concatenate([p[c].reshape(-1) for p in parts])) for c in range(5)]
@@ -203,13 +225,9 @@ def run_tubes(args, dist, rank, ws, local):
         ev1.record(stream)
         torch.cuda.synchronize()
     b.check()
-    ms = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(ev0.elapsed_time(ev1), dist)
     clocks = cs.summary()
-    mlups = nodes * args.steps * ws / (ms / 1e3) / 1e6
+    mlups = whole_job_rate(nodes * args.steps, ws, ms / 1e3)
     e2e = None
     if not args.no_e2e:
         hf = [t.pin_memory() for t in fields]
@@ -229,9 +247,10 @@ def run_tubes(args, dist, rank, ws, local):
     hbm_peak, peak_kind = _peaks()
     upd_s = nodes * args.steps / (ms / 1e3)
     gbs = 304 * upd_s / 1e9
-    fp64_peak = 152 * 2 * 2 * 2.07
-    alu = {"bound": "alu", "achieved": FLOPS_PER_UPDATE_F32S_FP64PART * upd_s / 1e9, "peak": fp64_peak,
-           "unit": "GFLOP/s", "traffic": None, "peak_kind": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"}
+    fp64_peak = 152 * 2 * 2.07
+    alu = {"bound": "alu", "achieved": FP64_OPS_PER_UPDATE_F32S * upd_s / 1e9, "peak": fp64_peak,
+           "unit": "G FP64 op/s", "traffic": None,
+           "peak_kind": "derived: 152 SM x 2 FP64 op/clk x 2.07 GHz (measured 2.05 DFMA/clk/SM)"}
     alu["frac"] = alu["achieved"] / fp64_peak
     hbm = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
            "traffic": None, "peak_kind": peak_kind, "note": "streaming-equivalent bytes (304 B/update); the tubes "
@@ -302,7 +321,7 @@ def run_ours(args):
     from paper_1211_3286_gb300 import inputs as I
     from paper_1211_3286_gb300.lattice import Lattice
 
-    if args.workload == "tubes":
+    if args.workload in ("tubes", "tubes_small"):
         return run_tubes(args, dist, rank, ws, local)
     if args.workload == "adjoint":
         return run_adjoint(args, dist, rank, ws, local)
@@ -332,14 +351,10 @@ def run_ours(args):
     if dist is not None:
         dist.barrier()
     lat.check()
-    ms = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(ev0.elapsed_time(ev1), dist)
     clocks = cs.summary()
     per_launch_s = ms / 1e3 / args.steps
-    mlups = nodes * args.steps * ws / (ms / 1e3) / 1e6
+    mlups = whole_job_rate(nodes * args.steps, ws, ms / 1e3)
 
     # end to end through the C ABI with pinned host buffers: upload the initial
     # fields, run the steps, read the final fields back
@@ -356,12 +371,8 @@ def run_ours(args):
         from paper_1211_3286_gb300 import _lib as L
         import ctypes
         L.rlb_get_fields(lat.handle, *[ctypes.c_void_p(o.data_ptr()) for o in outs], L.RLB_HOST)
-        dt = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([dt], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": nodes * args.steps * ws / dt / 1e6, "unit": "MLUPS",
+        dt = reduce_max(time.perf_counter() - t0, dist)
+        e2e = {"value": whole_job_rate(nodes * args.steps, ws, dt), "unit": "MLUPS",
                "h2d_bytes_per_step": 5 * nodes * 8 / args.steps, "d2h_bytes_per_step": 6 * nodes * 8 / args.steps,
                "what": "rlb_set_fields(host) + rlb_step(K) + rlb_get_fields(host), pinned buffers"}
     lat.close()
@@ -372,12 +383,14 @@ def run_ours(args):
            "traffic": None, "peak_kind": peak_kind}
     roof = hbm
     if wl["precision"] == "fp64":
-        # FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz (unit counts and max clock)
-        fp64_peak = 152 * 2 * 2 * 2.07
-        gfl = FLOPS_PER_UPDATE_F64 * nodes / per_launch_s / 1e9
-        alu = {"bound": "alu", "achieved": gfl, "peak": fp64_peak, "unit": "GFLOP/s", "frac": gfl / fp64_peak,
-               "traffic": None, "peak_kind": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
-               "hbm_frac": gbs / hbm_peak}
+        # The FP64 pipe bounds this kernel: 152 SMs x 2 FP64 instructions per clock x 2.07 GHz.
+        # Algorithmic FP64 operations per node update (add, mul, fma = 1; sqrt, reciprocal = 1).
+        fp64_peak = 152 * 2 * 2.07
+        gops = FP64_OPS_PER_UPDATE * nodes / per_launch_s / 1e9
+        alu = {"bound": "alu", "achieved": gops, "peak": fp64_peak, "unit": "G FP64 op/s", "frac": gops / fp64_peak,
+               "traffic": None, "peak_kind": "derived: 152 SM x 2 FP64 op/clk x 2.07 GHz (measured 2.05 DFMA/clk/SM)",
+               "flops": {"achieved_gflops": FLOPS_PER_UPDATE_F64 * nodes / per_launch_s / 1e9,
+                         "peak_gflops": 2 * fp64_peak}, "hbm_frac": gbs / hbm_peak}
         if alu["frac"] > hbm["frac"]:
             roof = alu
     if rank == 0:
@@ -390,7 +403,7 @@ def run_ours(args):
                 "roofline": roof, "hbm_roofline": hbm, "clocks": clocks, "e2e": e2e,
                 "gpu_launches": args.steps}
         if not args.no_cpu_baseline and ws == 1:
-            line["cpu_baseline"] = cpu_baseline(15.0)
+            line["cpu_baseline"] = cpu_baseline(args.ref_seconds)
         print(json.dumps(line))
 
 
@@ -403,6 +416,8 @@ def main():
     ap.add_argument("--workload", default="box256", choices=sorted(WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-seconds", type=float, default=20.0,
+                    help="CPU budget of the oracle sample (reference arm and cpu_baseline)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

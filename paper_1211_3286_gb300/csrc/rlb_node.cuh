@@ -167,29 +167,26 @@ __device__ __forceinline__ float d2f_trunc_bits(double x) {   // seed only: trun
                      ((hi & 0xfffffu) << 3) | (lo >> 29);
   return __uint_as_float(b);
 }
+__device__ __forceinline__ double widen_seed(float rf) {   // normal float -> double by moving bits
+  const unsigned rb = __float_as_uint(rf);
+  return __hiloint2double((int)((rb & 0x80000000u) | ((((rb >> 23) & 0xffu) + 896u) << 20) | ((rb & 0x7fffffu) >> 3)),
+                          (int)(rb << 29));
+}
 __device__ __forceinline__ double sqrt_seeded(double A) {
   float rf;
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(d2f_trunc_bits(A)));
-  const unsigned rb = __float_as_uint(rf);
-  // widen the seed by moving bits (normal range)
-  double y = __hiloint2double((int)((rb & 0x80000000u) | ((((rb >> 23) & 0xffu) + 896u) << 20) | ((rb & 0x7fffffu) >> 3)),
-                              (int)(rb << 29));
-  double e = fma(-A * y, y, 1.0);            // 1 - A y^2
-  y = fma(0.5 * y, e, y);                    // 1/sqrt(A) to ~2^-46
-  const double s = A * y;
-  const double d = fma(-s, s, A);            // A - s^2
-  return fma(0.5 * y, d, s);
+  const double y = widen_seed(rf);           // 1/sqrt(A) to ~2^-23
+  const double h = 0.5 * y;
+  double s = A * y;                          // sqrt(A) to ~2^-23
+  s = fma(h, fma(-s, s, A), s);              // s += h (A - s^2): ~2^-46
+  return fma(h, fma(-s, s, A), s);           // ~2^-69: FP64 rounding level
 }
 __device__ __forceinline__ double rcp_seeded(double x) {
   float rf;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(d2f_trunc_bits(x)));
-  const unsigned rb = __float_as_uint(rf);
-  double y = __hiloint2double((int)((rb & 0x80000000u) | ((((rb >> 23) & 0xffu) + 896u) << 20) | ((rb & 0x7fffffu) >> 3)),
-                              (int)(rb << 29));
-  double e = fma(-x, y, 1.0);
-  y = fma(y, e, y);
-  e = fma(-x, y, 1.0);
-  return fma(y, e, y);
+  const double y = widen_seed(rf);           // ~2^-23
+  const double e = fma(-x, y, 1.0);
+  return fma(y, fma(e, e, e), y);            // cubic step: ~2^-69
 }
 
 // Round-to-nearest-even narrowing of a double to float by moving bits (the
@@ -364,7 +361,7 @@ __device__ __forceinline__ double sum3_to_f64(const float (&v)[3]) {
 }
 
 // Exact level sums of g: T00, M, and the axis / diagonal class sums.
-__device__ __forceinline__ bool exact_sums_g(const float (&g)[19], Sums3& S) {
+__device__ __forceinline__ int exact_sums_g(const float (&g)[19], Sums3& S) {
   const int E = max_exp19(g);
   const float sg[3] = {pow2_bits(E + 6), pow2_bits(E - 13), pow2_bits(E - 32)};
   float r[19];
@@ -390,10 +387,10 @@ __device__ __forceinline__ bool exact_sums_g(const float (&g)[19], Sums3& S) {
     S.My[L] = ((d[1] + d[3]) - (d[4] - d[7])) + d[8];
     S.Mz[L] = ((d[2] + d[5]) - (d[6] - d[7])) - d[8];
   }
-  return E == 255;
+  return E;
 }
 
-__device__ __forceinline__ bool exact_sum_f(const float (&f)[19], float (&N0)[3]) {
+__device__ __forceinline__ int exact_sum_f(const float (&f)[19], float (&N0)[3]) {
   const int E = max_exp19(f);
   const float sg[3] = {pow2_bits(E + 6), pow2_bits(E - 13), pow2_bits(E - 32)};
   float r[19];
@@ -412,7 +409,31 @@ __device__ __forceinline__ bool exact_sum_f(const float (&f)[19], float (&N0)[3]
              (((q[8] + q[9]) + (q[10] + q[11])) + ((q[12] + q[13]) + (q[14] + q[15])))) +
             ((q[16] + q[17]) + q[18]);
   }
-  return E == 255;
+  return E;
+}
+
+// The three level sums of one extraction are integer multiples of their grids
+// 2^-24 sigma_L (sigma_1 = 2^(E+6-127), sigma_2 = 2^-19 sigma_1, sigma_3 = 2^-38 sigma_1),
+// so the exact sum is K * 2^(E-56-127) with K = k1 2^38 + k2 2^19 + k3, |K| < 2^63.
+// The integers are read from the float bits (exact: each part is a multiple of its grid).
+__device__ __forceinline__ long long level_int(float v, int eg) {
+  const unsigned b = __float_as_uint(v);
+  const int es = (int)((b >> 23) & 0xffu);
+  const unsigned m = (b & 0x7fffffu) | 0x800000u;
+  int sh = 23 - (es - eg);
+  sh = sh < 0 ? 0 : (sh > 31 ? 31 : sh);
+  const long long k = es == 0 ? 0 : (long long)(m >> sh);
+  return (b >> 31) ? -k : k;
+}
+__device__ __forceinline__ long long levels_to_int(const float (&v)[3], int E) {
+  return (level_int(v[0], E - 18) << 38) + (level_int(v[1], E - 37) << 19) + level_int(v[2], E - 56);
+}
+// x * 2^e for a normal double whose scaled value stays normal (exponent add on the
+// bits); zero stays zero
+__device__ __forceinline__ double scale_pow2(double x, int e) {
+  const int hi = __double2hiint(x), lo = __double2loint(x);
+  const bool zero = ((hi & 0x7fffffff) | lo) == 0;
+  return __hiloint2double(zero ? hi : hi + (e << 20), lo);
 }
 
 // FP32-storage node collide: the conserved sums exact (above) and delivered in
@@ -422,19 +443,42 @@ template <bool MRT, bool QSEP>
 __device__ __forceinline__ bool node_collide_f32s(float (&f)[19], float (&g)[19], const StepConst& k) {
   Sums3 S;
   float N0p[3];
-  bool nonfinite = exact_sums_g(g, S);
-  nonfinite |= exact_sum_f(f, N0p);
+  const int Eg = exact_sums_g(g, S);
+  const int Ef = exact_sum_f(f, N0p);
+  // exact sums as integers K * 2^(E - 183); the recovery is homogeneous of degree 1
+  // in (T00, M) (u is scale free), so it runs on the unscaled K and scales after
+  const double Tu = __ll2double_rn(levels_to_int(S.T00, Eg));
+  const double Mxu = __ll2double_rn(levels_to_int(S.Mx, Eg));
+  const double Myu = __ll2double_rn(levels_to_int(S.My, Eg));
+  const double Mzu = __ll2double_rn(levels_to_int(S.Mz, Eg));
+  const double N0u = __ll2double_rn(levels_to_int(N0p, Ef));
   NodeMacro m;
-  m.T00 = sum3_to_f64(S.T00);
-  m.Mx = sum3_to_f64(S.Mx);
-  m.My = sum3_to_f64(S.My);
-  m.Mz = sum3_to_f64(S.Mz);
-  m.N0 = sum3_to_f64(N0p);
-  node_recover_fast(m);
-  m.bad |= nonfinite;
-
+  const double MM = fma(Mxu, Mxu, fma(Myu, Myu, Mzu * Mzu));
+  const double A = fma(scale_pow2(Tu, 2), Tu, -3.0 * MM);
+  const double sgu = fma(2.0, Tu, sqrt_seeded(A)) * (1.0 / 3.0);
+  const double is = rcp_seeded(sgu);
+  m.ux = Mxu * is;
+  m.uy = Myu * is;
+  m.uz = Mzu * is;
+  const double Pu = sgu - Tu;
+  m.u2 = MM * is * is;
+  m.bad = !(pos_finite_hi(A) && pos_finite_hi(Tu) && pos_finite_hi(Pu) &&
+            (unsigned)__double2hiint(m.u2) < 0x3ff00000u) || Eg == 255 || Ef == 255;
+  const int eg = Eg - 183, ef = Ef - 183;
+  // per-node equilibrium constants (they cancel, sigma ~ 4P): FP64, then one rounding
+  const double su2u = sgu * m.u2;
+  const double P3u = 3.0 * Pu;
+  const float su2 = d2f_rn_bits(scale_pow2(su2u, eg));
+  const float kg = d2f_rn_bits(scale_pow2(fma(-1.5, su2u, P3u), eg));
+  const float geq0 = d2f_rn_bits(scale_pow2(fma(-0.5, su2u, sgu - P3u), eg));
   const float ux = d2f_rn_bits(m.ux), uy = d2f_rn_bits(m.uy), uz = d2f_rn_bits(m.uz);
-  const float N0 = d2f_rn_bits(m.N0), sg = d2f_rn_bits(m.sigma), P = d2f_rn_bits(m.P);
+  const float N0 = d2f_rn_bits(scale_pow2(N0u, ef)), sg = d2f_rn_bits(scale_pow2(sgu, eg));
+  const float P = d2f_rn_bits(scale_pow2(Pu, eg));
+  if (QSEP) {
+    m.Mx = scale_pow2(Mxu, eg);
+    m.My = scale_pow2(Myu, eg);
+    m.Mz = scale_pow2(Mzu, eg);
+  }
   const float u2 = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
   float cu[9];
   pair_cu<float>(ux, uy, uz, cu);
@@ -454,12 +498,6 @@ __device__ __forceinline__ bool node_collide_f32s(float (&f)[19], float (&g)[19]
     }
   }
   {
-    // the two per-node equilibrium constants cancel (sigma ~ 4P): formed in FP64
-    const double su2d = m.sigma * m.u2;
-    const double P3d = 3.0 * m.P;
-    const float su2 = d2f_rn_bits(su2d);
-    const float kg = d2f_rn_bits(fma(-1.5, su2d, P3d));
-    const float geq0 = d2f_rn_bits(fma(-0.5, su2d, m.sigma - P3d));
     float KA = k.gA_k_f * kg, KD = k.gD_k_f * kg;
     const float SA = k.gA_s_f * sg, SD = k.gD_s_f * sg;
     const float AA = k.gA_a_f * sg, AD = k.gD_a_f * sg;
