@@ -60,14 +60,24 @@ def normal(seed, stream, count) -> np.ndarray:
 
 
 # ----------------------------------------------------------------------------- shock tube
-def shock_tube(L: int, P_left: float = 5.43e-3, P_right: float = 2.22e-3):
+# Sec. V.B moderately relativistic shock: P = 5.43 : 0.339 GeV fm^-3, T = 400 : 200 MeV
+MODERATE = dict(P_left=5.43e-3, P_right=0.339e-3, T_left=2.0, T_right=1.0)
+
+
+def shock_tube(L: int, P_left: float = 5.43e-3, P_right: float = 2.22e-3, T_left=None, T_right=None):
     """Quasi-1D Riemann problem along x on an L x 1 x 1 lattice.  Returns numpy
-    arrays e, ux, uy, uz, n of shape (1, 1, L) in (z, y, x) order."""
+    arrays e, ux, uy, uz, n of shape (1, 1, L) in (z, y, x) order.  Without
+    temperatures n = (e / e_L)^(3/4); with T_left / T_right, n = P / T normalised to
+    n_L = 1 (the paper's n = P / T of Sec. III.B and V.B)."""
     i = np.arange(L)
     P = np.where(i < L // 2, P_left, P_right).astype(np.float64)
     e = 3.0 * P
     eL = 3.0 * P_left
-    n = (e / eL) ** 0.75
+    if T_left is None:
+        n = (e / eL) ** 0.75
+    else:
+        Tn = np.where(i < L // 2, T_left, T_right).astype(np.float64)
+        n = (P / Tn) / (P_left / T_left)
     z = np.zeros_like(e)
     sh = (1, 1, L)
     return e.reshape(sh), z.reshape(sh), z.copy().reshape(sh), z.copy().reshape(sh), n.reshape(sh)

@@ -259,3 +259,47 @@ def test_full_size_256_sampled_step_and_conservation(precision):
     tol = 1e-13 if precision == "fp64" else 1e-6
     assert max(abs(a - b) / s for a, b, s in zip(t1, t0, scale)) < tol
     lat.close()
+
+
+# ----------------------------------------------------------------------------- moderately relativistic shock (Sec. V.B)
+@pytest.mark.parametrize("collision", ["mrt", "bgk"])
+def test_moderately_relativistic_shock_fp64(collision):
+    """P = 5.43 : 0.339, T = 400 : 200 MeV (n = P/T), tau_v = 3, tau_e = tau_eps =
+    0.5 + (tau_v - 0.5)/30: plateau speed ~0.54, parity with the oracle to 1e-12."""
+    e, ux, uy, uz, n = (torch.from_numpy(a) for a in I.shock_tube(600, **I.MODERATE))
+    te = 0.5 + 2.5 / 30.0
+    gpu, ref, _, _ = _run_both(e, ux, uy, uz, n, 300, collision, (3.0, 3.0, te, te, 0.0),
+                               ("zero_gradient", "periodic", "periodic"))
+    err = field_errors(gpu, ref)
+    assert max(err.values()) < TOL64, err
+    assert float(gpu["ux"].max()) > 0.5
+
+
+def test_moderately_relativistic_breakdown_flagged_like_the_oracle():
+    """tau_v = 1.5 with a = 1/30: the oracle meets a non-physical node; the GPU reports
+    RLB_ENONPHYS within the same run (the device flag, no fault)."""
+    from paper_1211_3286_gb300 import _lib as L
+    from paper_1211_3286_gb300.lattice import Lattice
+    e, ux, uy, uz, n = (torch.from_numpy(a) for a in I.shock_tube(800, **I.MODERATE))
+    te = 0.5 + 1.0 / 30.0
+    prm = O.Params(collision="mrt", tau_f=1.5, tau_v=1.5, tau_e=te, tau_eps=te,
+                   bc=(O.ZERO_GRADIENT, O.PERIODIC, O.PERIODIC))
+    f, g = O.init_populations(e, torch.stack([ux, uy, uz]), n)
+    first_bad = None
+    for t in range(1, 301):
+        try:
+            f, g = O.step(f, g, prm)
+        except O.NonPhysical:
+            first_bad = t
+            break
+    assert first_bad is not None
+    lat = Lattice((1, 1, 800), collision="mrt", tau_f=1.5, tau_v=1.5, tau_e=te, tau_eps=te,
+                  bc=("zero_gradient", "periodic", "periodic"))
+    lat.set_fields(e.cuda(), ux.cuda(), uy.cuda(), uz.cuda(), n.cuda())
+    lat.step(first_bad - 1)
+    lat.check()                       # still physical one step before the oracle's failure
+    lat.step(1)
+    with pytest.raises(L.RlbError) as ex:
+        lat.check()
+    assert ex.value.code == L.RLB_ENONPHYS
+    lat.close()
