@@ -77,12 +77,35 @@ def d3q19():
     return E, W
 
 
-def opposite():
+def d2q9():
+    """D2Q9 velocity set (embedded in 3-D with e_z = 0) and weights of the MRT model
+    of Sec. V.A (Eqs. 30-35): rest (w = 4/9), four axis links (1/9), four
+    diagonals (1/36); c_s^2 = 1/3.  Order: 0 rest; 1..4 = +x, -x, +y, -y;
+    5..8 = (1,1), (-1,-1), (1,-1), (-1,1) (the opposite of odd link a is a + 1)."""
+    links = [(0, 0, 0), (1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (1, 1, 0), (-1, -1, 0), (1, -1, 0), (-1, 1, 0)]
+    E = torch.tensor(links, dtype=DT)
+    W = torch.empty(9, dtype=DT)
+    for a, c in enumerate(links):
+        W[a] = {0: 4.0 / 9.0, 1: 1.0 / 9.0, 2: 1.0 / 36.0}[sum(x * x for x in c)]
+    return E, W
+
+
+def lattice(lat="d3q19"):
+    """(E, W) of a lattice given by name ("d3q19", "d2q9") or by its link count."""
+    if lat in ("d3q19", 19):
+        return d3q19()
+    if lat in ("d2q9", 9):
+        return d2q9()
+    raise ValueError(lat)
+
+
+def opposite(lat="d3q19"):
     """Index of the link opposite to each link (e_opp = -e)."""
-    E, _ = d3q19()
+    E, _ = lattice(lat)
+    Q = E.shape[0]
     opp = []
-    for a in range(19):
-        for b in range(19):
+    for a in range(Q):
+        for b in range(Q):
             if torch.equal(E[b], -E[a]):
                 opp.append(b)
                 break
@@ -95,32 +118,36 @@ def _edotu(E, u):
 
 
 def _bcast(w, like):
-    """Reshape a per-link vector (19,) to broadcast against (19, *grid)."""
-    return w.to(like.dtype).reshape((19,) + (1,) * (like.dim() - 1))
+    """Reshape a per-link vector (Q,) to broadcast against (Q, *grid)."""
+    return w.to(like.dtype).reshape((w.shape[0],) + (1,) * (like.dim() - 1))
 
 
 # ----------------------------------------------------------------------------- equilibria
-def f_eq(n, u):
+def f_eq(n, u, lat="d3q19"):
     """Number equilibrium, Eq. 7:
     f^eq_a = w_a n gamma [1 + e.u/c_s^2 + (e.u)^2/(2 c_s^4) - u^2/(2 c_s^2)]."""
-    E, W = d3q19()
+    E, W = lattice(lat)
     u2 = (u * u).sum(0)
     gamma = 1.0 / torch.sqrt(1.0 - u2)
     eu = _edotu(E, u)
     return _bcast(W, eu) * (n * gamma) * (1.0 + eu / CS2 + eu * eu / (2.0 * CS2 * CS2) - u2 / (2.0 * CS2))
 
 
-def g_eq(e, P, u):
-    """Energy-momentum equilibrium, Eqs. 8 (rest link) and 9 (moving links), with
-    sigma = (e + P) gamma^2."""
-    E, W = d3q19()
+def g_eq(e, P, u, lat="d3q19"):
+    """Energy-momentum equilibrium, with sigma = (e + P) gamma^2: D3Q19 rest link
+    Eq. 8, moving links Eq. 9; D2Q9 (Sec. V.A) rest link Eq. 32, moving links Eq. 33
+    (the same form as Eq. 9)."""
+    E, W = lattice(lat)
     u2 = (u * u).sum(0)
     gamma2 = 1.0 / (1.0 - u2)
     sigma = (e + P) * gamma2
     eu = _edotu(E, u)
     Wb = _bcast(W, eu)
     moving = Wb * sigma * (P / (sigma * CS2) + eu / CS2 + eu * eu / (2.0 * CS2 * CS2) - u2 / (2.0 * CS2))
-    rest = W[0] * sigma * (3.0 - P * (2.0 + 3.0 * CS2) / (sigma * CS2) - u2 / (2.0 * CS2))
+    if E.shape[0] == 19:
+        rest = W[0] * sigma * (3.0 - P * (2.0 + 3.0 * CS2) / (sigma * CS2) - u2 / (2.0 * CS2))
+    else:
+        rest = W[0] * sigma * (9.0 / 4.0 - P * (5.0 + 9.0 * CS2) / (4.0 * sigma * CS2) - u2 / (2.0 * CS2))
     out = moving.clone()
     out[0] = rest
     return out
@@ -130,14 +157,15 @@ def g_eq(e, P, u):
 def moments(f, g):
     """Eq. 10: N0 = n gamma = sum_a f_a, T00 = (e+P) gamma^2 - P = sum_a g_a,
     M = (e+P) gamma^2 u = sum_a e_a g_a.  Sums run over links in index order."""
-    E, _ = d3q19()
+    E, _ = lattice(g.shape[0])
+    Q = E.shape[0]
     N0 = f[0].clone()
     T00 = g[0].clone()
     M = torch.zeros((3,) + tuple(g.shape[1:]), dtype=g.dtype)
-    for a in range(1, 19):
+    for a in range(1, Q):
         N0 = N0 + f[a]
         T00 = T00 + g[a]
-    for a in range(19):
+    for a in range(Q):
         for i in range(3):
             if E[a, i] != 0:
                 M[i] = M[i] + E[a, i].item() * g[a]
@@ -186,9 +214,32 @@ def recover(N0, T00, M, check: bool = True) -> Fields:
 # ----------------------------------------------------------------------------- MRT
 MRT_ROWS = ["rho", "e", "eps", "jx", "qx", "jy", "qy", "jz", "qz",
             "pxx", "pixx", "pww", "piww", "pxy", "pyz", "pxz", "mx", "my", "mz"]
+MRT_ROWS_D2Q9 = ["rho", "e", "eps", "jx", "qx", "jy", "qy", "pxx", "pxy"]
 
 
-def mrt_matrix():
+def mrt_rows(lat="d3q19"):
+    return MRT_ROWS if lattice(lat)[0].shape[0] == 19 else MRT_ROWS_D2Q9
+
+
+def mrt_matrix_d2q9():
+    """9x9 moment matrix of the D2Q9 MRT model of Eqs. 30-35 (the basis the paper
+    takes from its Ref. [24]; Lallemand and Luo, Phys. Rev. E 61, 6546 (2000)):
+      rho = 1, e = 3|c|^2 - 4, eps = (9|c|^4 - 21|c|^2 + 8)/2, j_i = c_i,
+      q_i = (3|c|^2 - 5) c_i, p_xx = c_x^2 - c_y^2, p_xy = c_x c_y."""
+    E, _ = d2q9()
+    Mx = torch.zeros(9, 9, dtype=DT)
+    for a in range(9):
+        cx, cy = E[a, 0].item(), E[a, 1].item()
+        c2 = cx * cx + cy * cy
+        row = {"rho": 1.0, "e": 3.0 * c2 - 4.0, "eps": (9.0 * c2 * c2 - 21.0 * c2 + 8.0) / 2.0,
+               "jx": cx, "qx": (3.0 * c2 - 5.0) * cx, "jy": cy, "qy": (3.0 * c2 - 5.0) * cy,
+               "pxx": cx * cx - cy * cy, "pxy": cx * cy}
+        for k, name in enumerate(MRT_ROWS_D2Q9):
+            Mx[k, a] = row[name]
+    return Mx
+
+
+def mrt_matrix(lat="d3q19"):
     """19x19 moment matrix M of the D3Q19 MRT model (rows are polynomials of the
     link velocity c, after d'Humieres et al. 2002), replacing the D2Q9 matrix that
     Eqs. 30-35 take from the paper's Ref. [24]:
@@ -197,6 +248,8 @@ def mrt_matrix():
       p_ww = c_y^2 - c_z^2, pi_ww = (3|c|^2 - 5) p_ww, p_xy = c_x c_y,
       p_yz = c_y c_z, p_xz = c_x c_z, m_x = (c_y^2 - c_z^2) c_x,
       m_y = (c_z^2 - c_x^2) c_y, m_z = (c_x^2 - c_y^2) c_z."""
+    if lattice(lat)[0].shape[0] == 9:
+        return mrt_matrix_d2q9()
     E, _ = d3q19()
     Mx = torch.zeros(19, 19, dtype=DT)
     for a in range(19):
@@ -223,9 +276,9 @@ def mrt_matrix():
     return Mx
 
 
-def relaxation_diag(tau_v, tau_e, tau_eps, tau_q, like=None):
-    """Diagonal of S (the D3Q19 analogue of Eq. 31): conserved rho, j -> 1;
-    e -> 1/tau_e; eps -> 1/tau_eps; q -> 1/tau_q; p, pi, m -> 1/tau_v.
+def relaxation_diag(tau_v, tau_e, tau_eps, tau_q, like=None, lat="d3q19"):
+    """Diagonal of S (Eq. 31 for D2Q9 and its D3Q19 analogue): conserved rho, j -> 1;
+    e -> 1/tau_e; eps -> 1/tau_eps; q -> 1/tau_q; p (and for D3Q19 pi, m) -> 1/tau_v.
     Arguments may be Python floats or 0-d tensors (for autograd / complex step)."""
     def t(x):
         return x if torch.is_tensor(x) else torch.tensor(float(x), dtype=DT)
@@ -233,7 +286,7 @@ def relaxation_diag(tau_v, tau_e, tau_eps, tau_q, like=None):
     one = torch.ones((), dtype=tv.dtype)
     rate = {"rho": one, "jx": one, "jy": one, "jz": one,
             "e": 1.0 / te, "eps": 1.0 / tp, "qx": 1.0 / tq, "qy": 1.0 / tq, "qz": 1.0 / tq}
-    return torch.stack([rate.get(name, 1.0 / tv) * one for name in MRT_ROWS])
+    return torch.stack([rate.get(name, 1.0 / tv) * one for name in mrt_rows(lat)])
 
 
 # ----------------------------------------------------------------------------- collision
@@ -245,12 +298,13 @@ def collide_bgk(p, peq, tau):
 def collide_mrt(g, geq, S):
     """MRT relaxation of g, Eqs. 30 and 35 with delta_t = 1:
     m = M g, m^eq = M g^eq, m* = m - S (m - m^eq), g* = M^{-1} m*."""
-    Mx = mrt_matrix().to(g.dtype)
-    Minv = torch.linalg.inv(mrt_matrix()).to(g.dtype)
+    Q = g.shape[0]
+    Mx = mrt_matrix(Q).to(g.dtype)
+    Minv = torch.linalg.inv(mrt_matrix(Q)).to(g.dtype)
     shape = g.shape
-    m = Mx @ g.reshape(19, -1)
-    meq = Mx @ geq.reshape(19, -1)
-    mstar = m - S.to(g.dtype).reshape(19, 1) * (m - meq)
+    m = Mx @ g.reshape(Q, -1)
+    meq = Mx @ geq.reshape(Q, -1)
+    mstar = m - S.to(g.dtype).reshape(Q, 1) * (m - meq)
     return (Minv @ mstar).reshape(shape)
 
 
@@ -269,10 +323,10 @@ def stream_pull(pop, bc: Sequence[str]):
     arriving at node x is the post-collision one at x - e_a.  ``pop`` is laid out
     (19, nz, ny, nx); ``bc`` gives (bc_x, bc_y, bc_z).  Periodic axes wrap,
     zero-gradient axes clamp the source node into the domain."""
-    E, _ = d3q19()
+    E, _ = lattice(pop.shape[0])
     _, nz, ny, nx = pop.shape
     out = torch.empty_like(pop)
-    for a in range(19):
+    for a in range(pop.shape[0]):
         cx, cy, cz = (int(E[a, 0]), int(E[a, 1]), int(E[a, 2]))
         sx = _source_index(nx, cx, bc[0])
         sy = _source_index(ny, cy, bc[1])
@@ -291,14 +345,15 @@ class Params:
     tau_eps: float = 0.9
     tau_q: float = 0.0                  # <= 0 means tau_q = tau_v
     bc: tuple = (PERIODIC, PERIODIC, PERIODIC)
+    lattice: str = "d3q19"               # or "d2q9" (the MRT model of Sec. V.A)
 
     def tq(self):
         return self.tau_v if (not torch.is_tensor(self.tau_q) and self.tau_q <= 0) else self.tau_q
 
 
-def init_populations(e, u, n):
-    """Initial state: f = f^eq(n, u), g = g^eq(e, P = e/3, u) (Eqs. 7-9)."""
-    return f_eq(n, u), g_eq(e, e / 3.0, u)
+def init_populations(e, u, n, lat="d3q19"):
+    """Initial state: f = f^eq(n, u), g = g^eq(e, P = e/3, u) (Eqs. 7-9; 32-33 for D2Q9)."""
+    return f_eq(n, u, lat), g_eq(e, e / 3.0, u, lat)
 
 
 def collide(f, g, prm: Params, check: bool = True):
@@ -306,13 +361,13 @@ def collide(f, g, prm: Params, check: bool = True):
     (Eq. 5 for f; Eq. 6 or Eqs. 30/35 for g) at every node."""
     N0, T00, M = moments(f, g)
     fl = recover(N0, T00, M, check=check)
-    feq = f_eq(fl.n, fl.u)
-    geq = g_eq(fl.e, fl.P, fl.u)
+    feq = f_eq(fl.n, fl.u, prm.lattice)
+    geq = g_eq(fl.e, fl.P, fl.u, prm.lattice)
     fs = collide_bgk(f, feq, prm.tau_f)
     if prm.collision == "bgk":
         gs = collide_bgk(g, geq, prm.tau_v)
     elif prm.collision == "mrt":
-        S = relaxation_diag(prm.tau_v, prm.tau_e, prm.tau_eps, prm.tq())
+        S = relaxation_diag(prm.tau_v, prm.tau_e, prm.tau_eps, prm.tq(), lat=prm.lattice)
         gs = collide_mrt(g, geq, S)
     else:
         raise ValueError(prm.collision)
@@ -362,7 +417,7 @@ def misfit_and_gradient(e0, u0, n0, prm: Params, nsteps, P_target, u_target, w_P
     e0 = e0.detach().clone().requires_grad_(True)
     q = dataclasses.replace(prm, tau_v=tv, tau_e=te, tau_eps=tp,
                             tau_q=(tv if prm.tau_q <= 0 else float(prm.tau_q)))
-    f, g = init_populations(e0, u0, n0)
+    f, g = init_populations(e0, u0, n0, prm.lattice)
     f, g = run(f, g, q, nsteps, check=False)
     loss = profile_misfit(f, g, P_target, u_target, w_P, w_u)
     loss.backward()
