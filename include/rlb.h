@@ -50,6 +50,7 @@ extern "C" {
 
 /* lattice, equation of state, collision, boundary, precision, memory space */
 #define RLB_D3Q19               19
+#define RLB_D2Q9                 9   /* the MRT model of Sec. V.A (Eqs. 30-35): nz = 1, RLB_FP64 */
 #define RLB_EOS_ULTRAREL         1   /* P = e / 3 */
 #define RLB_BGK                  0   /* Eq. 6 for g */
 #define RLB_MRT                  1   /* Eqs. 30-35 (D3Q19 moment basis) for g */
@@ -75,7 +76,7 @@ extern "C" {
  */
 typedef struct rlb_config {
   int nx, ny, nz;
-  int lattice;      /* RLB_D3Q19 */
+  int lattice;      /* RLB_D3Q19 | RLB_D2Q9 */
   int eos;          /* RLB_EOS_ULTRAREL */
   int collision;    /* RLB_BGK | RLB_MRT */
   double tau_f, tau_v, tau_e, tau_eps, tau_q;
@@ -87,9 +88,12 @@ typedef struct rlb_config {
 typedef struct rlb_handle rlb_handle;
 
 /* Allocate a lattice on the current CUDA device.  Returns RLB_EINVAL for a
- * zero or negative extent, an unknown enum, or any tau <= 0.5; RLB_ENOMEM if the
- * two lattices (2 x 38 x nodes x 8 or 4 bytes) do not fit.  *out is set only on
- * success. */
+ * zero or negative extent, an unknown enum, any tau <= 0.5, or RLB_D2Q9 with
+ * nz != 1 or FP32 storage; RLB_ENOMEM if the two lattices (2 x 2Q x nodes x 8 or 4
+ * bytes, Q = 19 or 9 links) do not fit.  *out is set only on success.
+ * RLB_D2Q9 runs the D2Q9 model of Sec. V.A: rest equilibrium Eq. 32, moving links
+ * Eq. 33, MRT basis of Eqs. 30-35 with S of Eq. 31 (its field arrays have u_z = 0;
+ * rlb_set_fields rejects u_z != 0). */
 int rlb_create(const rlb_config* cfg, rlb_handle** out);
 
 /* Free the handle and its device memory (synchronises its stream).  NULL is a no-op. */
@@ -128,9 +132,9 @@ int rlb_get_fields(rlb_handle* h, double* e, double* P, double* ux, double* uy, 
  * collision).  out is host memory.  Synchronises. */
 int rlb_conserved_totals(rlb_handle* h, double out[5]);
 
-/* Number of bytes of one raw state: 2 x 19 x nodes x (8 for RLB_FP64, 4 for
- * RLB_FP32_STORAGE).  Layout: f[19][nz][ny][nx] followed by g[19][nz][ny][nx],
- * post-collision populations of the current time step. */
+/* Number of bytes of one raw state: 2 x Q x nodes x (8 for RLB_FP64, 4 for
+ * RLB_FP32_STORAGE), Q = 19 (D3Q19) or 9 (D2Q9).  Layout: f[Q][nz][ny][nx]
+ * followed by g[Q][nz][ny][nx], post-collision populations of the current time step. */
 size_t rlb_state_bytes(const rlb_handle* h);
 
 /* Copy the raw state out to / in from `where` memory of rlb_state_bytes(h)

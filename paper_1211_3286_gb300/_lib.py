@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(HERE, "_build", "librlb.so")
 
 RLB_OK, RLB_EINVAL, RLB_ENOMEM, RLB_ECUDA, RLB_ENONPHYS, RLB_ETIMEOUT = range(6)
 RLB_D3Q19 = 19
+RLB_D2Q9 = 9
 RLB_EOS_ULTRAREL = 1
 RLB_BGK, RLB_MRT = 0, 1
 RLB_PERIODIC, RLB_ZERO_GRADIENT = 0, 1

@@ -15,6 +15,7 @@ struct rlb_handle {
   cudaStream_t stream = nullptr;
   size_t nodes = 0;
   size_t esize = 8;
+  int Q = 19;                                      // links per distribution: 19 (D3Q19) or 9 (D2Q9)
   void* lat[2] = {nullptr, nullptr};
   int cur = 0;
   unsigned long long* d_bad = nullptr;   // smallest non-physical node index, ULLONG_MAX if none

@@ -109,15 +109,42 @@ __global__ void __launch_bounds__(kBlockX) k_step(const S* __restrict__ src, S* 
   }
 }
 
+// D2Q9 (FP64): node (x, y) pulls link a from (x - c_x, y - c_y).
+template <bool MRT, bool QSEP>
+__global__ void __launch_bounds__(kBlockX) k_step_d2q9(const double* __restrict__ src, double* __restrict__ dst,
+                                                       Geo geo, StepConst k, unsigned long long* __restrict__ bad) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= geo.nx) return;
+  const int y = blockIdx.y;
+  const int xs[3] = {src_minus(x, geo.nx, geo.bcx), x, src_plus(x, geo.nx, geo.bcx)};
+  const unsigned row[3] = {(unsigned)src_minus(y, geo.ny, geo.bcy) * (unsigned)geo.nx, (unsigned)y * (unsigned)geo.nx,
+                           (unsigned)src_plus(y, geo.ny, geo.bcy) * (unsigned)geo.nx};
+  double f[9], g[9];
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    const unsigned idx = row[1 - d2_cy(a)] + (unsigned)xs[1 - d2_cx(a)];
+    f[a] = __ldg(src + (unsigned long long)a * geo.plane + idx);
+    g[a] = __ldg(src + (9ull + a) * geo.plane + idx);
+  }
+  const bool b = node_collide_d2q9_f64<MRT, QSEP>(f, g, k);
+  const unsigned node = row[1] + (unsigned)x;
+  if (b) atomicMin(bad, (unsigned long long)node);
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    dst[(unsigned long long)a * geo.plane + node] = f[a];
+    dst[(9ull + a) * geo.plane + node] = g[a];
+  }
+}
+
 // Deterministic two-pass sum of (N0, T00, Mx, My, Mz) over all nodes.
-template <typename S>
+template <typename S, int Q = 19>
 __global__ void __launch_bounds__(kRedThreads) k_totals_part(const S* __restrict__ lat, unsigned long long nodes,
                                                              double* __restrict__ part) {
   double acc[5] = {0, 0, 0, 0, 0};
   for (unsigned long long i = blockIdx.x * (unsigned long long)kRedThreads + threadIdx.x; i < nodes;
        i += (unsigned long long)kRedBlocks * kRedThreads) {
     NodeMacro m;
-    stored_moments<S>(lat, nodes, i, m);
+    stored_moments<S, Q>(lat, nodes, i, m);
     acc[0] += m.N0; acc[1] += m.T00; acc[2] += m.Mx; acc[3] += m.My; acc[4] += m.Mz;
   }
   __shared__ double sh[5][kRedThreads];
@@ -166,6 +193,17 @@ bool qsep(const rlb_config& c) { return c.collision == RLB_MRT && c.tau_q > 0 &&
 template <typename S>
 cudaError_t launch_step(rlb_handle* h, const void* src, void* dst, cudaStream_t st) {
   const Geo geo = make_geo(h);
+  if (h->Q == 9) {
+    const int bx = h->nodes <= 152ull * 128ull * 2ull ? 32 : kBlockX;
+    dim3 grid2((geo.nx + bx - 1) / bx, geo.ny, 1);
+    const bool mrt2 = h->cfg.collision == RLB_MRT, q2 = qsep(h->cfg);
+    const double* s2 = (const double*)src;
+    double* d2 = (double*)dst;
+    if (!mrt2) k_step_d2q9<false, false><<<grid2, bx, 0, st>>>(s2, d2, geo, h->k, h->d_bad);
+    else if (!q2) k_step_d2q9<true, false><<<grid2, bx, 0, st>>>(s2, d2, geo, h->k, h->d_bad);
+    else k_step_d2q9<true, true><<<grid2, bx, 0, st>>>(s2, d2, geo, h->k, h->d_bad);
+    return cudaGetLastError();
+  }
   // small lattices (a 1600-node tube) spread over more SMs with one warp per block:
   // the FP64 pipe of an SM serves 2 lanes per clock, so fewer warps per SM means
   // shorter steps when the lattice cannot fill the GPU anyway
@@ -240,7 +278,10 @@ int validate_taus(double tau_f, double tau_v, double tau_e, double tau_eps, doub
 extern "C" int rlb_create(const rlb_config* cfg, rlb_handle** out) {
   if (!cfg || !out) return fail(nullptr, RLB_EINVAL, "null argument");
   if (cfg->nx <= 0 || cfg->ny <= 0 || cfg->nz <= 0) return fail(nullptr, RLB_EINVAL, "lattice extents must be > 0");
-  if (cfg->lattice != RLB_D3Q19) return fail(nullptr, RLB_EINVAL, "only RLB_D3Q19 is supported");
+  if (cfg->lattice != RLB_D3Q19 && cfg->lattice != RLB_D2Q9)
+    return fail(nullptr, RLB_EINVAL, "lattice must be RLB_D3Q19 or RLB_D2Q9");
+  if (cfg->lattice == RLB_D2Q9 && (cfg->nz != 1 || cfg->precision != RLB_FP64))
+    return fail(nullptr, RLB_EINVAL, "RLB_D2Q9 needs nz == 1 and RLB_FP64");
   if (cfg->eos != RLB_EOS_ULTRAREL) return fail(nullptr, RLB_EINVAL, "only RLB_EOS_ULTRAREL (P = e/3) is supported");
   if (cfg->collision != RLB_BGK && cfg->collision != RLB_MRT) return fail(nullptr, RLB_EINVAL, "unknown collision");
   if (cfg->precision != RLB_FP64 && cfg->precision != RLB_FP32_STORAGE)
@@ -261,9 +302,11 @@ extern "C" int rlb_create(const rlb_config* cfg, rlb_handle** out) {
   h->stream = (cudaStream_t)cfg->stream;
   h->nodes = nodes;
   h->esize = cfg->precision == RLB_FP64 ? 8 : 4;
-  h->k = make_step_const(cfg->tau_f, cfg->tau_v, cfg->tau_e, cfg->tau_eps, cfg->tau_q, cfg->collision == RLB_MRT);
+  h->Q = cfg->lattice == RLB_D2Q9 ? 9 : 19;
+  h->k = make_step_const(cfg->tau_f, cfg->tau_v, cfg->tau_e, cfg->tau_eps, cfg->tau_q, cfg->collision == RLB_MRT,
+                         h->Q);
   cudaGetDevice(&h->device);
-  const size_t bytes = 38 * h->nodes * h->esize;
+  const size_t bytes = 2 * (size_t)h->Q * h->nodes * h->esize;
   for (int i = 0; i < 2; ++i) {
     if (cudaMalloc(&h->lat[i], bytes) != cudaSuccess) {
       cudaGetLastError();
@@ -329,7 +372,9 @@ extern "C" int rlb_set_fields(rlb_handle* h, const double* e, const double* ux, 
   const int spare = 1 - h->cur;
   const unsigned long long none = ULLONG_MAX;
   RLB_CUDA(h, cudaMemcpyAsync(h->d_bad, &none, sizeof none, cudaMemcpyHostToDevice, h->stream));
-  if (h->esize == 8)
+  if (h->Q == 9)
+    k_init<double, 9><<<grid_for(N), 256, 0, h->stream>>>((double*)h->lat[spare], N, de, dx, dy, dz, dn, h->d_bad);
+  else if (h->esize == 8)
     k_init<double><<<grid_for(N), 256, 0, h->stream>>>((double*)h->lat[spare], N, de, dx, dy, dz, dn, h->d_bad);
   else
     k_init<float><<<grid_for(N), 256, 0, h->stream>>>((float*)h->lat[spare], N, de, dx, dy, dz, dn, h->d_bad);
@@ -374,7 +419,10 @@ extern "C" int rlb_get_fields(rlb_handle* h, double* e, double* P, double* ux, d
   if (where == RLB_DEVICE)
     for (int c = 0; c < 6; ++c)
       if (want[c]) dev[c] = want[c];
-  if (h->esize == 8)
+  if (h->Q == 9)
+    k_fields<double, 9><<<grid_for(N), 256, 0, h->stream>>>((const double*)h->lat[h->cur], N, dev[0], dev[1], dev[2],
+                                                             dev[3], dev[4], dev[5], h->d_bad);
+  else if (h->esize == 8)
     k_fields<double><<<grid_for(N), 256, 0, h->stream>>>((const double*)h->lat[h->cur], N, dev[0], dev[1], dev[2],
                                                           dev[3], dev[4], dev[5], h->d_bad);
   else
@@ -391,7 +439,9 @@ extern "C" int rlb_get_fields(rlb_handle* h, double* e, double* P, double* ux, d
 extern "C" int rlb_conserved_totals(rlb_handle* h, double out[5]) {
   if (!h || !out) return fail(h, RLB_EINVAL, "null argument");
   const size_t N = h->nodes;
-  if (h->esize == 8)
+  if (h->Q == 9)
+    k_totals_part<double, 9><<<kRedBlocks, kRedThreads, 0, h->stream>>>((const double*)h->lat[h->cur], N, h->d_part);
+  else if (h->esize == 8)
     k_totals_part<double><<<kRedBlocks, kRedThreads, 0, h->stream>>>((const double*)h->lat[h->cur], N, h->d_part);
   else
     k_totals_part<float><<<kRedBlocks, kRedThreads, 0, h->stream>>>((const float*)h->lat[h->cur], N, h->d_part);
@@ -404,7 +454,7 @@ extern "C" int rlb_conserved_totals(rlb_handle* h, double out[5]) {
   return RLB_OK;
 }
 
-extern "C" size_t rlb_state_bytes(const rlb_handle* h) { return h ? 38 * h->nodes * h->esize : 0; }
+extern "C" size_t rlb_state_bytes(const rlb_handle* h) { return h ? 2 * (size_t)h->Q * h->nodes * h->esize : 0; }
 
 extern "C" int rlb_save_state(rlb_handle* h, void* buf, int where) {
   if (!h || !buf) return fail(h, RLB_EINVAL, "null argument");

@@ -69,10 +69,13 @@ struct StepConst {
   float ce_f, cp_f, cq_f;
 };
 
+// q = 19 (D3Q19: weights 1/3, 1/18, 1/36; MRT row norms e 2394, eps 252, q 40) or
+// q = 9 (D2Q9: weights 4/9, 1/9, 1/36; norms e 36, eps 36, q 12).
 inline StepConst make_step_const(double tau_f, double tau_v, double tau_e, double tau_eps, double tau_q,
-                                 bool mrt) {
+                                 bool mrt, int q = 19) {
   StepConst k{};
-  const double wA = 1.0 / 18.0, wD = 1.0 / 36.0, w0 = 1.0 / 3.0;
+  const bool d2 = q == 9;
+  const double wA = d2 ? 1.0 / 9.0 : 1.0 / 18.0, wD = 1.0 / 36.0, w0 = d2 ? 4.0 / 9.0 : 1.0 / 3.0;
   k.omf = 1.0 / tau_f;
   k.omf1 = 1.0 - k.omf;
   k.fA_k = k.omf * wA;
@@ -92,9 +95,9 @@ inline StepConst make_step_const(double tau_f, double tau_v, double tau_e, doubl
   k.gD_a = 3.0 * k.omv * wD;
   if (mrt) {
     const double tq = tau_q > 0 ? tau_q : tau_v;
-    k.ce = (1.0 / tau_e - k.omv) / 2394.0;
-    k.cp = (1.0 / tau_eps - k.omv) / 252.0;
-    k.cq = (1.0 / tq - k.omv) / 40.0;
+    k.ce = (1.0 / tau_e - k.omv) / (d2 ? 36.0 : 2394.0);
+    k.cp = (1.0 / tau_eps - k.omv) / (d2 ? 36.0 : 252.0);
+    k.cq = (1.0 / tq - k.omv) / (d2 ? 12.0 : 40.0);
   }
   k.omf_f = (float)k.omf; k.omf1_f = (float)k.omf1;
   k.fA_k_f = (float)k.fA_k; k.fD_k_f = (float)k.fD_k; k.f0_k_f = (float)k.f0_k;
@@ -567,6 +570,133 @@ __device__ __forceinline__ void node_equilibrium(double e, double ux, double uy,
 #pragma unroll
   for (int p = 0; p < 9; ++p) {
     const double w = p < 3 ? wA : wD;
+    const double c2 = 4.5 * cu[p] * cu[p];
+    const double fe = w * (kf + N0 * c2), fo = w * 3.0 * N0 * cu[p];
+    const double ge = w * (kg + sigma * c2), go = w * 3.0 * sigma * cu[p];
+    f[2 * p + 1] = fe + fo;
+    f[2 * p + 2] = fe - fo;
+    g[2 * p + 1] = ge + go;
+    g[2 * p + 2] = ge - go;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// D2Q9 (the MRT model of Sec. V.A, Eqs. 30-35), FP64.  Link order: 0 rest;
+// pairs p = 0..3 hold links 2p+1 (direction c_p) and 2p+2 (-c_p): p0 +x, p1 +y,
+// p2 (1,1), p3 (1,-1).  Rest equilibrium Eq. 32: g^eq_0 = sigma - (8/3) P - (2/3)
+// sigma u^2; moving links Eq. 33 (the Eq. 9 form with the D2Q9 weights).  Class
+// sums of g^eq: axis (4/3) P + sigma u^2 / 3, diagonal P / 3 + sigma u^2 / 3.  MRT
+// rows e = 3|c|^2 - 4 (-4, -1, 2), eps (4, -2, 1), q_i = (3|c|^2 - 5) c_i.
+__host__ __device__ constexpr int d2_cx(int a) {
+  constexpr int t[9] = {0, 1, -1, 0, 0, 1, -1, 1, -1};
+  return t[a];
+}
+__host__ __device__ constexpr int d2_cy(int a) {
+  constexpr int t[9] = {0, 0, 0, 1, -1, 1, -1, -1, 1};
+  return t[a];
+}
+
+template <typename S>
+__device__ __forceinline__ void node_moments_d2q9(const S (&f)[9], const S (&g)[9], double (&dp)[4], double& Sa,
+                                                  double& Sd, NodeMacro& m) {
+  double sp[4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const double a = (double)g[2 * p + 1], b = (double)g[2 * p + 2];
+    sp[p] = a + b;
+    dp[p] = a - b;
+  }
+  Sa = sp[0] + sp[1];
+  Sd = sp[2] + sp[3];
+  m.T00 = ((double)g[0] + Sa) + Sd;
+  m.Mx = (dp[0] + dp[2]) + dp[3];
+  m.My = (dp[1] + dp[2]) - dp[3];
+  m.Mz = 0.0;
+  m.N0 = (double)f[0] + ((((double)f[1] + (double)f[2]) + ((double)f[3] + (double)f[4])) +
+                         (((double)f[5] + (double)f[6]) + ((double)f[7] + (double)f[8])));
+}
+
+template <bool MRT, bool QSEP>
+__device__ __forceinline__ bool node_collide_d2q9_f64(double (&f)[9], double (&g)[9], const StepConst& k) {
+  double dp[4], Sa, Sd;
+  NodeMacro m;
+  node_moments_d2q9<double>(f, g, dp, Sa, Sd, m);
+  node_recover_fast(m);
+  double cu[4];
+  cu[0] = m.ux; cu[1] = m.uy; cu[2] = m.ux + m.uy; cu[3] = m.ux - m.uy;
+  {
+    const double kf = fma(-1.5 * m.N0, m.u2, m.N0);
+    const double KA = k.fA_k * kf, KD = k.fD_k * kf;
+    const double SA = k.fA_s * m.N0, SD = k.fD_s * m.N0;
+    const double AA = k.fA_a * m.N0, AD = k.fD_a * m.N0;
+    f[0] = fma(k.omf1, f[0], k.f0_k * kf);
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const bool ax = p < 2;
+      const double ev = fma(ax ? SA : SD, cu[p] * cu[p], ax ? KA : KD);
+      const double od = (ax ? AA : AD) * cu[p];
+      f[2 * p + 1] = fma(k.omf1, f[2 * p + 1], ev + od);
+      f[2 * p + 2] = fma(k.omf1, f[2 * p + 2], ev - od);
+    }
+  }
+  {
+    const double su2 = m.sigma * m.u2;
+    const double kg = fma(-1.5, su2, 3.0 * m.P);
+    const double geq0 = fma(-2.0 / 3.0, su2, fma(-8.0 / 3.0, m.P, m.sigma));
+    double KA = k.gA_k * kg, KD = k.gD_k * kg;
+    const double SA = k.gA_s * m.sigma, SD = k.gD_s * m.sigma;
+    const double AA = k.gA_a * m.sigma, AD = k.gD_a * m.sigma;
+    double g0n = fma(k.omv1, g[0], k.omv * geq0);
+    double dq[4] = {0.0, 0.0, 0.0, 0.0};
+    if (MRT) {
+      const double n0 = g[0] - geq0;
+      const double nA = Sa - fma(1.0 / 3.0, su2, (4.0 / 3.0) * m.P);
+      const double nD = Sd - (m.P + su2) * (1.0 / 3.0);
+      const double ne = fma(2.0, nD, fma(-4.0, n0, -nA));
+      const double np = fma(-2.0, nA, fma(4.0, n0, nD));
+      const double ae = k.ce * ne, ap = k.cp * np;
+      g0n = g0n + 4.0 * (ae - ap);
+      KA = KA + fma(2.0, ap, ae);
+      KD = KD - fma(2.0, ae, ap);
+      if (QSEP) {
+        const double aqx = k.cq * (fma(-2.0, dp[0], dp[2] + dp[3]) + m.Mx);
+        const double aqy = k.cq * (fma(-2.0, dp[1], dp[2] - dp[3]) + m.My);
+        dq[0] = 2.0 * aqx;
+        dq[1] = 2.0 * aqy;
+        dq[2] = -(aqx + aqy);
+        dq[3] = -(aqx - aqy);
+      }
+    }
+    g[0] = g0n;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const bool ax = p < 2;
+      const double ev = fma(ax ? SA : SD, cu[p] * cu[p], ax ? KA : KD);
+      double od = (ax ? AA : AD) * cu[p];
+      if (MRT && QSEP) od += dq[p];
+      g[2 * p + 1] = fma(k.omv1, g[2 * p + 1], ev + od);
+      g[2 * p + 2] = fma(k.omv1, g[2 * p + 2], ev - od);
+    }
+  }
+  return m.bad;
+}
+
+// D2Q9 equilibrium populations of given fields (Eqs. 7, 32, 33), FP64.
+__device__ __forceinline__ void node_equilibrium_d2q9(double e, double ux, double uy, double n, double (&f)[9],
+                                                      double (&g)[9]) {
+  const double u2 = fma(ux, ux, uy * uy);
+  const double g2 = 1.0 / (1.0 - u2);
+  const double P = e * (1.0 / 3.0);
+  const double sigma = (e + P) * g2;
+  const double N0 = n * sqrt(g2);
+  const double cu[4] = {ux, uy, ux + uy, ux - uy};
+  const double kf = N0 * (1.0 - 1.5 * u2);
+  const double kg = 3.0 * P - 1.5 * sigma * u2;
+  f[0] = (4.0 / 9.0) * kf;
+  g[0] = sigma - (8.0 / 3.0) * P - (2.0 / 3.0) * sigma * u2;
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const double w = p < 2 ? 1.0 / 9.0 : 1.0 / 36.0;
     const double c2 = 4.5 * cu[p] * cu[p];
     const double fe = w * (kf + N0 * c2), fo = w * 3.0 * N0 * cu[p];
     const double ge = w * (kg + sigma * c2), go = w * 3.0 * sigma * cu[p];

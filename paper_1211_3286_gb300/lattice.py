@@ -14,6 +14,7 @@ from . import _lib as L
 _BC = {"periodic": L.RLB_PERIODIC, "zero_gradient": L.RLB_ZERO_GRADIENT}
 _COLL = {"bgk": L.RLB_BGK, "mrt": L.RLB_MRT}
 _PREC = {"fp64": L.RLB_FP64, "fp32": L.RLB_FP32_STORAGE}
+_LAT = {"d3q19": L.RLB_D3Q19, "d2q9": L.RLB_D2Q9}
 
 
 def _where(t: torch.Tensor):
@@ -36,13 +37,14 @@ class Lattice:
     """A (nz, ny, nx) D3Q19 lattice with f and g populations on the current GPU."""
 
     def __init__(self, shape, collision="mrt", tau_f=0.9, tau_v=0.9, tau_e=0.9, tau_eps=0.9, tau_q=0.0,
-                 bc=("periodic", "periodic", "periodic"), precision="fp64", stream=None):
+                 bc=("periodic", "periodic", "periodic"), precision="fp64", stream=None, lattice="d3q19"):
         nz, ny, nx = shape
         self.shape = (nz, ny, nx)
         self.precision = precision
+        self.Q = 9 if lattice == "d2q9" else 19
         cfg = L.rlb_config()
         cfg.nx, cfg.ny, cfg.nz = nx, ny, nz
-        cfg.lattice, cfg.eos = L.RLB_D3Q19, L.RLB_EOS_ULTRAREL
+        cfg.lattice, cfg.eos = _LAT[lattice], L.RLB_EOS_ULTRAREL
         cfg.collision = _COLL[collision]
         cfg.tau_f, cfg.tau_v, cfg.tau_e, cfg.tau_eps, cfg.tau_q = tau_f, tau_v, tau_e, tau_eps, tau_q
         for a in range(3):
@@ -95,9 +97,9 @@ class Lattice:
         return L.rlb_conserved_totals(self._h)
 
     def state(self, device="cuda"):
-        """Raw post-collision populations as a (38, nz, ny, nx) tensor (f then g)."""
+        """Raw post-collision populations as a (2Q, nz, ny, nx) tensor (f then g)."""
         dt = torch.float64 if self.precision == "fp64" else torch.float32
-        t = torch.empty((38,) + self.shape, dtype=dt, device=device)
+        t = torch.empty((2 * self.Q,) + self.shape, dtype=dt, device=device)
         L.rlb_save_state(self._h, _ptr(t), _where(t))
         return t
 

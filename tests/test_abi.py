@@ -54,7 +54,8 @@ def _cfg(**kw):
 
 
 @pytest.mark.parametrize("kw, what", [
-    (dict(nx=0), "extents"), (dict(lattice=9), "D3Q19"), (dict(collision=7), "collision"),
+    (dict(nx=0), "extents"), (dict(lattice=27), "lattice must be"), (dict(lattice=9, nz=2), "D2Q9"),
+    (dict(lattice=9, precision=1), "D2Q9"), (dict(collision=7), "collision"),
     (dict(precision=5), "precision"), (dict(taus=(0.5, 0.9, 0.55, 0.8, 0.0)), "tau_f"),
     (dict(taus=(0.9, 0.9, 0.4, 0.8, 0.0)), "tau_e"), (dict(taus=(0.9, 0.9, 0.55, 0.8, 0.3)), "tau_q"),
 ])

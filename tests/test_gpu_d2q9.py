@@ -1,0 +1,87 @@
+"""GPU parity of the D2Q9 MRT model (Sec. V.A, Eqs. 30-35; RLB_D2Q9) against the
+oracle's D2Q9 statement: the paper's 4-wide open tube with the relaxation-time
+cases A-D, 2-D periodic and zero-gradient boxes, separate tau_q, conservation."""
+import numpy as np
+import pytest
+import torch
+
+import oracle.rlb_oracle as O
+from paper_1211_3286_gb300 import inputs as I
+from tests.helpers import field_errors, oracle_bc, oracle_fields
+
+pytestmark = pytest.mark.gpu
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1211_3286_gb300 import build
+    build.build()
+
+
+def _run(e, ux, uy, n, steps, collision, taus, bc):
+    from paper_1211_3286_gb300.lattice import Lattice
+    tf, tv, te, tp, tq = taus
+    lat = Lattice(tuple(e.shape), collision=collision, tau_f=tf, tau_v=tv, tau_e=te, tau_eps=tp, tau_q=tq, bc=bc,
+                  lattice="d2q9")
+    z = torch.zeros_like(e)
+    lat.set_fields(e.cuda(), ux.cuda(), uy.cuda(), z.cuda(), n.cuda())
+    lat.step(steps)
+    gpu, tot = lat.fields("cuda"), lat.totals()
+    lat.close()
+    prm = O.Params(collision=collision, tau_f=tf, tau_v=tv, tau_e=te, tau_eps=tp, tau_q=tq, bc=oracle_bc(bc),
+                   lattice="d2q9")
+    f, g = O.run(*O.init_populations(e, torch.stack([ux, uy, z]), n, "d2q9"), prm, steps)
+    return gpu, oracle_fields(f, g), tot, O.conserved_totals(f, g)
+
+
+def _cases(tv, a=1.0 / 20.0):
+    """Sec. V.B: A: all equal; B: tau_q - 1/2 = a (tau_v - 1/2); C: tau_e; D: tau_e = tau_eps."""
+    s = 0.5 + a * (tv - 0.5)
+    return {"A": (tv, tv, tv, tv, tv), "B": (tv, tv, tv, tv, s), "C": (tv, tv, s, tv, tv), "D": (tv, tv, s, s, tv)}
+
+
+@pytest.mark.parametrize("case", ["A", "B", "C", "D"])
+def test_d2q9_tube_cases(case):
+    """4 x L tube (periodic across, zero-gradient ends), shock initial state."""
+    L = 320
+    e, ux, uy, uz, n = (torch.from_numpy(a) for a in I.shock_tube(L))
+    e2, n2 = e.expand(1, 4, L).contiguous(), n.expand(1, 4, L).contiguous()
+    z = torch.zeros_like(e2)
+    gpu, ref, _, _ = _run(e2, z, z.clone(), n2, 250, "mrt", _cases(1.4)[case],
+                          ("zero_gradient", "periodic", "periodic"))
+    err = field_errors(gpu, ref)
+    assert max(err.values()) < TOL64, err
+
+
+@pytest.mark.parametrize("bc", [("periodic", "periodic", "periodic"), ("zero_gradient", "zero_gradient", "periodic")])
+def test_d2q9_box(bc):
+    e, ux, uy, uz, n = I.periodic_box(None, seed=71, shape=(1, 37, 150))
+    gpu, ref, tot, tref = _run(e, ux, uy, n, 40, "mrt", (0.8, 0.9, 0.6, 1.1, 1.3), bc)
+    err = field_errors(gpu, ref)
+    assert max(err.values()) < TOL64, err
+    if bc[0] == "periodic":
+        scale = [float(tref[0])] + [float(tref[1])] * 4
+        assert max(abs(a - float(b)) / s for a, b, s in zip(tot, tref, scale)) < 1e-13
+
+
+def test_d2q9_bgk_box():
+    e, ux, uy, uz, n = I.periodic_box(None, seed=72, shape=(1, 9, 33))
+    gpu, ref, _, _ = _run(e, ux, uy, n, 30, "bgk", (0.7, 0.9, 0.9, 0.9, 0.0), ("periodic",) * 3)
+    assert max(field_errors(gpu, ref).values()) < TOL64
+
+
+def test_d2q9_rejects_invalid_setups():
+    from paper_1211_3286_gb300 import _lib as L
+    from paper_1211_3286_gb300.lattice import Lattice
+    with pytest.raises(L.RlbError):
+        Lattice((2, 4, 8), lattice="d2q9")
+    with pytest.raises(L.RlbError):
+        Lattice((1, 4, 8), lattice="d2q9", precision="fp32")
+    lat = Lattice((1, 4, 8), lattice="d2q9")
+    one = torch.ones((1, 4, 8), dtype=torch.float64)
+    with pytest.raises(L.RlbError):
+        lat.set_fields(0.01 * one, 0 * one, 0 * one, 0.1 * one, one)   # u_z != 0
+    lat.close()
