@@ -58,6 +58,8 @@ extern "C" {
 #define RLB_ZERO_GRADIENT        1   /* "open" end: a pull from outside takes the edge node */
 #define RLB_FP64                 0   /* populations stored and updated in FP64 */
 #define RLB_FP32_STORAGE         1   /* populations stored in FP32; sums, recovery, gamma in FP64 */
+#define RLB_CORR_NONE            0
+#define RLB_CORR_C7              1   /* Eq. 37 with C_7 of Eq. 38 added to the m_7 = p_xx moment */
 #define RLB_HOST                 0
 #define RLB_DEVICE               1
 
@@ -73,6 +75,14 @@ extern "C" {
  *   tau_q    energy-flux moment time, MRT only; <= 0 means tau_q = tau_v.
  *   stream   a cudaStream_t (NULL = legacy default stream) on which all work of
  *            this handle is enqueued.
+ *   correction  RLB_CORR_C7 adds the error-correction term of Eqs. 37-38 to the
+ *            D2Q9 MRT collision: m* = m - S (m - m^eq) + (1 - s_7/2) C_7 e_7 with
+ *            C_7 = 2 [u dx(c_s^2 sigma - P) - c_s^2 sigma u dx(gamma)/gamma
+ *                     - u dx(sigma u^2) + u^2 theta dx(sigma u)],
+ *            theta = 1 + 1/((e/P + 1) gamma^2 - 1), the flow along x (the paper's z),
+ *            central differences of the fields pulled at the neighbours (a
+ *            zero-gradient end reuses the edge value).  Each step then runs two
+ *            kernels (fields, then the corrected collide).
  */
 typedef struct rlb_config {
   int nx, ny, nz;
@@ -83,6 +93,7 @@ typedef struct rlb_config {
   int bc[3];        /* per axis x, y, z: RLB_PERIODIC | RLB_ZERO_GRADIENT */
   int precision;    /* RLB_FP64 | RLB_FP32_STORAGE */
   void* stream;
+  int correction;   /* RLB_CORR_NONE | RLB_CORR_C7 (RLB_D2Q9 + RLB_MRT only, flow along x) */
 } rlb_config;
 
 typedef struct rlb_handle rlb_handle;

@@ -346,6 +346,7 @@ class Params:
     tau_q: float = 0.0                  # <= 0 means tau_q = tau_v
     bc: tuple = (PERIODIC, PERIODIC, PERIODIC)
     lattice: str = "d3q19"               # or "d2q9" (the MRT model of Sec. V.A)
+    correction: bool = False             # D2Q9 MRT only: the C_7 term of Eqs. 37-38 (flow along x)
 
     def tq(self):
         return self.tau_v if (not torch.is_tensor(self.tau_q) and self.tau_q <= 0) else self.tau_q
@@ -368,10 +369,53 @@ def collide(f, g, prm: Params, check: bool = True):
         gs = collide_bgk(g, geq, prm.tau_v)
     elif prm.collision == "mrt":
         S = relaxation_diag(prm.tau_v, prm.tau_e, prm.tau_eps, prm.tq(), lat=prm.lattice)
-        gs = collide_mrt(g, geq, S)
+        if prm.correction:
+            gs = collide_mrt_corrected(g, geq, S, fl, prm.bc[0])
+        else:
+            gs = collide_mrt(g, geq, S)
     else:
         raise ValueError(prm.collision)
     return fs, gs
+
+
+def _ddx(q, bc_x):
+    """Central difference along x (the tube axis, last dimension), delta_x = 1; a
+    zero-gradient end uses the edge value for the missing neighbour, a periodic axis
+    wraps."""
+    if bc_x == PERIODIC:
+        qp, qm = torch.roll(q, -1, dims=-1), torch.roll(q, 1, dims=-1)
+    else:
+        qp = torch.cat([q[..., 1:], q[..., -1:]], dim=-1)
+        qm = torch.cat([q[..., :1], q[..., :-1]], dim=-1)
+    return 0.5 * (qp - qm)
+
+
+def correction_c7(fl: Fields, bc_x):
+    """Eq. 38 with the flow along x (the paper's z):
+    C_7 = 2 dt [u dx(c_s^2 sigma - P) - c_s^2 sigma gamma^-1 u dx(gamma) - u dx(sigma u^2)
+               + u^2 theta dx(sigma u)],   theta = 1 + 1 / ((e/P + 1) gamma^2 - 1)."""
+    sg, P, gam, u = fl.sigma, fl.P, fl.gamma, fl.u[0]
+    theta = 1.0 + 1.0 / ((fl.e / P + 1.0) * gam * gam - 1.0)
+    return 2.0 * (u * _ddx(CS2 * sg - P, bc_x) - CS2 * sg / gam * u * _ddx(gam, bc_x)
+                  - u * _ddx(sg * u * u, bc_x) + u * u * theta * _ddx(sg * u, bc_x))
+
+
+def collide_mrt_corrected(g, geq, S, fl: Fields, bc_x):
+    """Eq. 37: m* = m - S (m - m^eq) + (I - S/2) C with C_7 of Eq. 38 the only nonzero
+    entry; m_7 is the D2Q9 moment with m^eq_7 = sigma (u_x^2 - u_y^2) (row 'pxx')."""
+    Q = g.shape[0]
+    if Q != 9:
+        raise ValueError("the C_7 correction is defined for the D2Q9 model")
+    Mx = mrt_matrix(Q).to(g.dtype)
+    Minv = torch.linalg.inv(mrt_matrix(Q)).to(g.dtype)
+    shape = g.shape
+    m = Mx @ g.reshape(Q, -1)
+    meq = Mx @ geq.reshape(Q, -1)
+    Sd = S.to(g.dtype)
+    mstar = m - Sd.reshape(Q, 1) * (m - meq)
+    k7 = MRT_ROWS_D2Q9.index("pxx")
+    mstar[k7] = mstar[k7] + (1.0 - Sd[k7] / 2.0) * correction_c7(fl, bc_x).reshape(-1)
+    return (Minv @ mstar).reshape(shape)
 
 
 def step(f, g, prm: Params, check: bool = True):

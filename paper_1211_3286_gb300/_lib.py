@@ -20,6 +20,7 @@ RLB_BGK, RLB_MRT = 0, 1
 RLB_PERIODIC, RLB_ZERO_GRADIENT = 0, 1
 RLB_FP64, RLB_FP32_STORAGE = 0, 1
 RLB_HOST, RLB_DEVICE = 0, 1
+RLB_CORR_NONE, RLB_CORR_C7 = 0, 1
 
 _STATUS = {0: "RLB_OK", 1: "RLB_EINVAL", 2: "RLB_ENOMEM", 3: "RLB_ECUDA", 4: "RLB_ENONPHYS", 5: "RLB_ETIMEOUT"}
 
@@ -35,7 +36,8 @@ class rlb_config(ctypes.Structure):
                 ("lattice", ctypes.c_int), ("eos", ctypes.c_int), ("collision", ctypes.c_int),
                 ("tau_f", ctypes.c_double), ("tau_v", ctypes.c_double), ("tau_e", ctypes.c_double),
                 ("tau_eps", ctypes.c_double), ("tau_q", ctypes.c_double),
-                ("bc", ctypes.c_int * 3), ("precision", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("bc", ctypes.c_int * 3), ("precision", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("correction", ctypes.c_int)]
 
 
 class rlb_batch_desc(ctypes.Structure):

@@ -109,26 +109,73 @@ __global__ void __launch_bounds__(kBlockX) k_step(const S* __restrict__ src, S* 
   }
 }
 
-// D2Q9 (FP64): node (x, y) pulls link a from (x - c_x, y - c_y).
-template <bool MRT, bool QSEP>
-__global__ void __launch_bounds__(kBlockX) k_step_d2q9(const double* __restrict__ src, double* __restrict__ dst,
-                                                       Geo geo, StepConst k, unsigned long long* __restrict__ bad) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= geo.nx) return;
-  const int y = blockIdx.y;
+// D2Q9 pull of the 9 f and 9 g arriving at node (x, y).
+__device__ __forceinline__ unsigned pull_d2q9(const double* __restrict__ src, const Geo& geo, int x, int y,
+                                              double (&f)[9], double (&g)[9]) {
   const int xs[3] = {src_minus(x, geo.nx, geo.bcx), x, src_plus(x, geo.nx, geo.bcx)};
   const unsigned row[3] = {(unsigned)src_minus(y, geo.ny, geo.bcy) * (unsigned)geo.nx, (unsigned)y * (unsigned)geo.nx,
                            (unsigned)src_plus(y, geo.ny, geo.bcy) * (unsigned)geo.nx};
-  double f[9], g[9];
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
     const unsigned idx = row[1 - d2_cy(a)] + (unsigned)xs[1 - d2_cx(a)];
     f[a] = __ldg(src + (unsigned long long)a * geo.plane + idx);
     g[a] = __ldg(src + (9ull + a) * geo.plane + idx);
   }
-  const bool b = node_collide_d2q9_f64<MRT, QSEP>(f, g, k);
-  const unsigned node = row[1] + (unsigned)x;
+  return row[1] + (unsigned)x;
+}
+
+// Fields of the pulled D2Q9 state for the C_7 gradients (Eq. 38): per node
+// c_s^2 sigma - P, gamma, sigma u_x^2, sigma u_x.
+__global__ void __launch_bounds__(kBlockX) k_macro_d2q9(const double* __restrict__ src, double* __restrict__ q,
+                                                        Geo geo) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= geo.nx) return;
+  double f[9], g[9], dp[4], Sa, Sd;
+  const unsigned node = pull_d2q9(src, geo, x, blockIdx.y, f, g);
+  NodeMacro m;
+  node_moments_d2q9<double>(f, g, dp, Sa, Sd, m);
+  node_recover_fast(m);
+  const double su = m.sigma * m.ux;
+  q[node] = fma(1.0 / 3.0, m.sigma, -m.P);
+  q[geo.plane + node] = 1.0 / sqrt(1.0 - m.u2);
+  q[2 * geo.plane + node] = su * m.ux;
+  q[3 * geo.plane + node] = su;
+}
+
+// D2Q9 (FP64): node (x, y) pulls link a from (x - c_x, y - c_y).  With CORR the
+// C_7 term of Eqs. 37-38 is added to the m_7 = p_xx moment of the result.
+template <bool MRT, bool QSEP, bool CORR>
+__global__ void __launch_bounds__(kBlockX) k_step_d2q9(const double* __restrict__ src, double* __restrict__ dst,
+                                                       Geo geo, StepConst k, unsigned long long* __restrict__ bad,
+                                                       const double* __restrict__ q) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= geo.nx) return;
+  const int y = blockIdx.y;
+  double f[9], g[9];
+  const unsigned node = pull_d2q9(src, geo, x, y, f, g);
+  NodeMacro m;
+  const bool b = node_collide_d2q9_f64<MRT, QSEP>(f, g, k, m);
   if (b) atomicMin(bad, (unsigned long long)node);
+  if (CORR) {
+    // neighbours along x: a zero-gradient end reuses the edge node, a periodic axis wraps
+    const unsigned rowy = (unsigned)y * (unsigned)geo.nx;
+    const unsigned xm = rowy + (unsigned)(x > 0 ? x - 1 : (geo.bcx ? 0 : geo.nx - 1));
+    const unsigned xp = rowy + (unsigned)(x < geo.nx - 1 ? x + 1 : (geo.bcx ? geo.nx - 1 : 0));
+    const unsigned long long P = geo.plane;
+    const double d1 = 0.5 * (q[xp] - q[xm]);                    // dx(c_s^2 sigma - P)
+    const double d2 = 0.5 * (q[P + xp] - q[P + xm]);            // dx(gamma)
+    const double d3 = 0.5 * (q[2 * P + xp] - q[2 * P + xm]);    // dx(sigma u^2)
+    const double d4 = 0.5 * (q[3 * P + xp] - q[3 * P + xm]);    // dx(sigma u)
+    const double u = m.ux, gam = q[P + node];
+    const double theta = 1.0 + 1.0 / fma(4.0 * gam, gam, -1.0);   // e / P = 3
+    const double c7 = 2.0 * (u * d1 - (m.sigma * (1.0 / 3.0)) * (u / gam) * d2 - u * d3 + u * u * theta * d4);
+    // m_7 = p_xx (row c_x^2 - c_y^2, norm 4): (1 - s_7/2) C_7 spread over the axis links
+    const double dq = 0.25 * (1.0 - 0.5 * k.omv) * c7;
+    g[1] += dq;
+    g[2] += dq;
+    g[3] -= dq;
+    g[4] -= dq;
+  }
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
     dst[(unsigned long long)a * geo.plane + node] = f[a];
@@ -199,9 +246,17 @@ cudaError_t launch_step(rlb_handle* h, const void* src, void* dst, cudaStream_t 
     const bool mrt2 = h->cfg.collision == RLB_MRT, q2 = qsep(h->cfg);
     const double* s2 = (const double*)src;
     double* d2 = (double*)dst;
-    if (!mrt2) k_step_d2q9<false, false><<<grid2, bx, 0, st>>>(s2, d2, geo, h->k, h->d_bad);
-    else if (!q2) k_step_d2q9<true, false><<<grid2, bx, 0, st>>>(s2, d2, geo, h->k, h->d_bad);
-    else k_step_d2q9<true, true><<<grid2, bx, 0, st>>>(s2, d2, geo, h->k, h->d_bad);
+    if (h->cfg.correction == RLB_CORR_C7) {
+      k_macro_d2q9<<<grid2, bx, 0, st>>>(s2, h->d_macro, geo);
+      if (!q2) k_step_d2q9<true, false, true><<<grid2, bx, 0, st>>>(s2, d2, geo, h->k, h->d_bad, h->d_macro);
+      else k_step_d2q9<true, true, true><<<grid2, bx, 0, st>>>(s2, d2, geo, h->k, h->d_bad, h->d_macro);
+    } else if (!mrt2) {
+      k_step_d2q9<false, false, false><<<grid2, bx, 0, st>>>(s2, d2, geo, h->k, h->d_bad, nullptr);
+    } else if (!q2) {
+      k_step_d2q9<true, false, false><<<grid2, bx, 0, st>>>(s2, d2, geo, h->k, h->d_bad, nullptr);
+    } else {
+      k_step_d2q9<true, true, false><<<grid2, bx, 0, st>>>(s2, d2, geo, h->k, h->d_bad, nullptr);
+    }
     return cudaGetLastError();
   }
   // small lattices (a 1600-node tube) spread over more SMs with one warp per block:
@@ -282,6 +337,9 @@ extern "C" int rlb_create(const rlb_config* cfg, rlb_handle** out) {
     return fail(nullptr, RLB_EINVAL, "lattice must be RLB_D3Q19 or RLB_D2Q9");
   if (cfg->lattice == RLB_D2Q9 && (cfg->nz != 1 || cfg->precision != RLB_FP64))
     return fail(nullptr, RLB_EINVAL, "RLB_D2Q9 needs nz == 1 and RLB_FP64");
+  if (cfg->correction != RLB_CORR_NONE &&
+      (cfg->correction != RLB_CORR_C7 || cfg->lattice != RLB_D2Q9 || cfg->collision != RLB_MRT))
+    return fail(nullptr, RLB_EINVAL, "RLB_CORR_C7 needs RLB_D2Q9 and RLB_MRT");
   if (cfg->eos != RLB_EOS_ULTRAREL) return fail(nullptr, RLB_EINVAL, "only RLB_EOS_ULTRAREL (P = e/3) is supported");
   if (cfg->collision != RLB_BGK && cfg->collision != RLB_MRT) return fail(nullptr, RLB_EINVAL, "unknown collision");
   if (cfg->precision != RLB_FP64 && cfg->precision != RLB_FP32_STORAGE)
@@ -314,6 +372,12 @@ extern "C" int rlb_create(const rlb_config* cfg, rlb_handle** out) {
       return fail(nullptr, RLB_ENOMEM, "cannot allocate the two lattices");
     }
   }
+  if (cfg->correction == RLB_CORR_C7 && cudaMalloc(&h->d_macro, 4 * h->nodes * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    h->d_macro = nullptr;
+    rlb_destroy(h);
+    return fail(nullptr, RLB_ENOMEM, "cannot allocate the correction fields");
+  }
   if (cudaMalloc(&h->d_bad, sizeof(unsigned long long)) != cudaSuccess ||
       cudaMalloc(&h->d_part, (kRedBlocks * 5 + 8) * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
@@ -338,6 +402,7 @@ extern "C" void rlb_destroy(rlb_handle* h) {
   if (h->d_bad) cudaFree(h->d_bad);
   if (h->d_part) cudaFree(h->d_part);
   if (h->d_stage) cudaFree(h->d_stage);
+  if (h->d_macro) cudaFree(h->d_macro);
   delete h;
 }
 

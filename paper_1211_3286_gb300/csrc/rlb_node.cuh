@@ -617,9 +617,9 @@ __device__ __forceinline__ void node_moments_d2q9(const S (&f)[9], const S (&g)[
 }
 
 template <bool MRT, bool QSEP>
-__device__ __forceinline__ bool node_collide_d2q9_f64(double (&f)[9], double (&g)[9], const StepConst& k) {
+__device__ __forceinline__ bool node_collide_d2q9_f64(double (&f)[9], double (&g)[9], const StepConst& k,
+                                                      NodeMacro& m) {
   double dp[4], Sa, Sd;
-  NodeMacro m;
   node_moments_d2q9<double>(f, g, dp, Sa, Sd, m);
   node_recover_fast(m);
   double cu[4];

@@ -85,3 +85,42 @@ def test_d2q9_rejects_invalid_setups():
     with pytest.raises(L.RlbError):
         lat.set_fields(0.01 * one, 0 * one, 0 * one, 0.1 * one, one)   # u_z != 0
     lat.close()
+
+
+@pytest.mark.parametrize("bcx", ["zero_gradient", "periodic"])
+def test_d2q9_c7_correction(bcx):
+    """Eqs. 37-38 (RLB_CORR_C7): the moderately relativistic shock (n = P/T) on a 4-wide
+    tube with tau_v = 3, tau_e = tau_eps = 0.5 + (tau_v - 0.5)/30, corrected m_7;
+    FP64 parity with the oracle's corrected collision."""
+    from paper_1211_3286_gb300.lattice import Lattice
+    L, T = 300, 200
+    e, ux, uy, uz, n = (torch.from_numpy(a) for a in I.shock_tube(L, **I.MODERATE))
+    e2, n2 = e.expand(1, 4, L).contiguous(), n.expand(1, 4, L).contiguous()
+    z = torch.zeros_like(e2)
+    te = 0.5 + 2.5 / 30.0
+    bc = (bcx, "periodic", "periodic")
+    lat = Lattice((1, 4, L), collision="mrt", tau_f=3.0, tau_v=3.0, tau_e=te, tau_eps=te, bc=bc, lattice="d2q9",
+                  correction=True)
+    lat.set_fields(e2.cuda(), z.cuda(), z.cuda(), z.cuda(), n2.cuda())
+    lat.step(T)
+    gpu = lat.fields("cuda")
+    lat.close()
+    prm = O.Params(collision="mrt", tau_f=3.0, tau_v=3.0, tau_e=te, tau_eps=te, bc=oracle_bc(bc), lattice="d2q9",
+                   correction=True)
+    f, g = O.run(*O.init_populations(e2, torch.stack([z, z, z]), n2, "d2q9"), prm, T)
+    ref = oracle_fields(f, g)
+    err = field_errors(gpu, ref)
+    assert max(err.values()) < TOL64, err
+    # the correction is active: the uncorrected run differs
+    fu, gu = O.run(*O.init_populations(e2, torch.stack([z, z, z]), n2, "d2q9"),
+                   O.dataclasses.replace(prm, correction=False), T)
+    assert float((O.fields(fu, gu).P - ref["P"]).abs().max()) > 1e-6 * float(ref["P"].max())
+
+
+def test_c7_rejected_outside_d2q9_mrt():
+    from paper_1211_3286_gb300 import _lib as L
+    from paper_1211_3286_gb300.lattice import Lattice
+    with pytest.raises(L.RlbError):
+        Lattice((1, 4, 8), lattice="d3q19", correction=True)
+    with pytest.raises(L.RlbError):
+        Lattice((1, 4, 8), lattice="d2q9", collision="bgk", correction=True)

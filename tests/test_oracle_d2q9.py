@@ -177,3 +177,50 @@ def test_d2q9_shock_tube_4x800_plateau():
     assert abs(float(fl.u[0, 0, 0, L // 2]) / vs - 1) < 1e-3
     assert abs(float(fl.P[0, 0, L // 2]) / Ps - 1) < 1e-3
     assert float(fl.u[1].abs().max()) < 1e-15
+
+
+# ----------------------------------------------------------------------------- C_7 correction (Eqs. 37-38)
+def test_c7_vanishes_for_uniform_flow_and_at_rest():
+    """Every term of Eq. 38 carries u and a gradient: a uniform moving state and a fluid
+    at rest with a pressure bump are unchanged by the correction."""
+    L = 40
+    base = dict(collision="mrt", tau_f=0.9, tau_v=3.0, tau_e=0.6, tau_eps=0.6, lattice="d2q9", bc=ZG)
+    e = torch.full((1, 4, L), 0.012, dtype=torch.float64)
+    u = torch.zeros((3, 1, 4, L), dtype=torch.float64)
+    u[0] = 0.3
+    f, g = O.init_populations(e, u, torch.ones_like(e), "d2q9")
+    a = O.run(f, g, O.Params(**base), 20)
+    b = O.run(f, g, O.Params(correction=True, **base), 20)
+    assert torch.equal(a[1], b[1])
+    x = torch.arange(L, dtype=torch.float64)
+    e2 = (0.012 * (1 + 0.1 * torch.exp(-((x - 20) / 4) ** 2))).expand(1, 4, L).contiguous()
+    f, g = O.init_populations(e2, torch.zeros((3, 1, 4, L), dtype=torch.float64), torch.ones_like(e2), "d2q9")
+    a = O.collide(f, g, O.Params(**base))
+    b = O.collide(f, g, O.Params(correction=True, **base))
+    assert torch.equal(a[1], b[1])
+
+
+def test_c7_only_changes_m7_and_keeps_conservation():
+    """The correction enters only the m_7 row (Eq. 37 with C_{0..6,8} = 0): the other
+    eight moments of the post-collision state are unchanged and the periodic totals stay
+    conserved."""
+    L = 48
+    x = torch.arange(L, dtype=torch.float64)
+    e = (0.012 * (1 + 0.2 * torch.sin(2 * math.pi * x / L))).expand(1, 4, L).contiguous()
+    u = torch.zeros((3, 1, 4, L), dtype=torch.float64)
+    u[0] = 0.25 * torch.cos(2 * math.pi * x / L)
+    base = dict(collision="mrt", tau_f=0.9, tau_v=3.0, tau_e=0.6, tau_eps=0.6, lattice="d2q9", bc=(O.PERIODIC,) * 3)
+    f, g = O.init_populations(e, u, torch.ones_like(e), "d2q9")
+    _, ga = O.collide(f, g, O.Params(**base))
+    _, gb = O.collide(f, g, O.Params(correction=True, **base))
+    M = O.mrt_matrix("d2q9")
+    dm = M @ (gb - ga).reshape(9, -1)
+    k7 = O.MRT_ROWS_D2Q9.index("pxx")
+    assert dm[k7].abs().max() > 1e-8
+    others = torch.cat([dm[:k7], dm[k7 + 1:]])
+    assert others.abs().max() < 1e-15 * float(ga.abs().max()) * 20
+    t0 = O.conserved_totals(f, g)
+    fr, gr = O.run(f, g, O.Params(correction=True, **base), 60)
+    t1 = O.conserved_totals(fr, gr)
+    scale = torch.tensor([t0[0], t0[1], t0[1], t0[1], t0[1]])
+    assert ((t1 - t0).abs() / scale).max() < 1e-13
