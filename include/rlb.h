@@ -83,6 +83,11 @@ extern "C" {
  *            central differences of the fields pulled at the neighbours (a
  *            zero-gradient end reuses the edge value).  Each step then runs two
  *            kernels (fields, then the corrected collide).
+ *   eta_over_s  > 0 selects the paper's fixed-eta/s relaxation (Sec. II and III.B):
+ *            per node and step, tau_g = 1/2 + eta / (c_s^2 (e + P) gamma) with
+ *            eta = (eta/s) s, s = 4 n - n ln(n / n_eq), n_eq = 16 T^3 / pi^2 and
+ *            T = P / n; tau_v is then unused and tau_f <= 0 means tau_f = tau_g
+ *            (the Fig. 1 cases); n must be given in the same units as P.
  */
 typedef struct rlb_config {
   int nx, ny, nz;
@@ -94,6 +99,7 @@ typedef struct rlb_config {
   int precision;    /* RLB_FP64 | RLB_FP32_STORAGE */
   void* stream;
   int correction;   /* RLB_CORR_NONE | RLB_CORR_C7 (RLB_D2Q9 + RLB_MRT only, flow along x) */
+  double eta_over_s; /* > 0: per-node tau_g from eta/s (RLB_BGK, RLB_D3Q19, RLB_FP64); 0: constant taus */
 } rlb_config;
 
 typedef struct rlb_handle rlb_handle;

@@ -347,6 +347,8 @@ class Params:
     bc: tuple = (PERIODIC, PERIODIC, PERIODIC)
     lattice: str = "d3q19"               # or "d2q9" (the MRT model of Sec. V.A)
     correction: bool = False             # D2Q9 MRT only: the C_7 term of Eqs. 37-38 (flow along x)
+    eta_over_s: float = 0.0              # > 0: BGK tau_g per node from eta/s (Sec. II, III.B); tau_v unused
+                                         # then, and tau_f <= 0 means tau_f = tau_g
 
     def tq(self):
         return self.tau_v if (not torch.is_tensor(self.tau_q) and self.tau_q <= 0) else self.tau_q
@@ -364,6 +366,12 @@ def collide(f, g, prm: Params, check: bool = True):
     fl = recover(N0, T00, M, check=check)
     feq = f_eq(fl.n, fl.u, prm.lattice)
     geq = g_eq(fl.e, fl.P, fl.u, prm.lattice)
+    if prm.eta_over_s > 0:
+        if prm.collision != "bgk":
+            raise ValueError("eta/s-derived relaxation times are implemented for the BGK model")
+        tg = tau_from_eta_over_s(prm.eta_over_s, fl)
+        tf = tg if (not torch.is_tensor(prm.tau_f) and prm.tau_f <= 0) else prm.tau_f
+        return collide_bgk(f, feq, tf), collide_bgk(g, geq, tg)
     fs = collide_bgk(f, feq, prm.tau_f)
     if prm.collision == "bgk":
         gs = collide_bgk(g, geq, prm.tau_v)
@@ -416,6 +424,23 @@ def collide_mrt_corrected(g, geq, S, fl: Fields, bc_x):
     k7 = MRT_ROWS_D2Q9.index("pxx")
     mstar[k7] = mstar[k7] + (1.0 - Sd[k7] / 2.0) * correction_c7(fl, bc_x).reshape(-1)
     return (Minv @ mstar).reshape(shape)
+
+
+D_G = 16.0  # gluon degeneracy d_G of Sec. III.B
+
+
+def entropy_density(n, T):
+    """s = 4 n - n ln(lambda), lambda = n / n_eq, n_eq = d_G T^3 / pi^2 (Sec. III.B)."""
+    n_eq = D_G * T ** 3 / math.pi ** 2
+    return 4.0 * n - n * torch.log(n / n_eq)
+
+
+def tau_from_eta_over_s(eta_s, fl: Fields):
+    """Relaxation time from a fixed eta/s: eta = (tau - 1/2) c_s^2 (e + P) gamma (Sec. II,
+    after Eq. 10) with eta = (eta/s) s and the ideal-gas temperature T = P / n."""
+    T = fl.P / fl.n
+    eta = eta_s * entropy_density(fl.n, T)
+    return 0.5 + eta / (CS2 * (fl.e + fl.P) * fl.gamma)
 
 
 def step(f, g, prm: Params, check: bool = True):

@@ -37,7 +37,7 @@ class rlb_config(ctypes.Structure):
                 ("tau_f", ctypes.c_double), ("tau_v", ctypes.c_double), ("tau_e", ctypes.c_double),
                 ("tau_eps", ctypes.c_double), ("tau_q", ctypes.c_double),
                 ("bc", ctypes.c_int * 3), ("precision", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("correction", ctypes.c_int)]
+                ("correction", ctypes.c_int), ("eta_over_s", ctypes.c_double)]
 
 
 class rlb_batch_desc(ctypes.Structure):

@@ -425,6 +425,7 @@ extern "C" int rlb_adjoint(rlb_handle* h, int nsteps, int checkpoint_every, cons
   if (where != RLB_HOST && where != RLB_DEVICE) return afail(h, RLB_EINVAL, "where must be RLB_HOST or RLB_DEVICE");
   if (h->esize != 8) return afail(h, RLB_EINVAL, "rlb_adjoint needs an RLB_FP64 lattice");
   if (h->Q != 19) return afail(h, RLB_EINVAL, "rlb_adjoint supports RLB_D3Q19 lattices");
+  if (h->cfg.eta_over_s > 0) return afail(h, RLB_EINVAL, "rlb_adjoint needs constant relaxation times");
   if (h->cfg.collision == RLB_MRT && h->cfg.tau_q > 0 && h->cfg.tau_q != h->cfg.tau_v)
     return afail(h, RLB_EINVAL, "rlb_adjoint needs tau_q tied to tau_v (tau_q <= 0)");
   const bool mrt = h->cfg.collision == RLB_MRT;

@@ -78,7 +78,7 @@ __device__ __forceinline__ void pull19(const S* __restrict__ base, unsigned long
   }
 }
 
-template <typename S, bool MRT, bool QSEP>
+template <typename S, bool MRT, bool QSEP, bool ETA = false>
 __global__ void __launch_bounds__(kBlockX) k_step(const S* __restrict__ src, S* __restrict__ dst, Geo geo,
                                                   StepConst k, unsigned long long* __restrict__ bad) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(kBlockX) k_step(const S* __restrict__ src, S* 
   pull19<S>(src, geo.plane, xs, row, f);
   pull19<S>(src + 19ull * geo.plane, geo.plane, xs, row, g);
   bool b;
-  if constexpr (sizeof(S) == 8) b = node_collide_f64<MRT, QSEP>(f, g, k);
+  if constexpr (sizeof(S) == 8) b = node_collide_f64<MRT, QSEP, ETA>(f, g, k);
   else b = node_collide_f32s<MRT, QSEP>(f, g, k);
   const unsigned node = row[1][1] + (unsigned)x;
   if (b) atomicMin(bad, (unsigned long long)node);
@@ -267,6 +267,12 @@ cudaError_t launch_step(rlb_handle* h, const void* src, void* dst, cudaStream_t 
   const bool mrt = h->cfg.collision == RLB_MRT, q = qsep(h->cfg);
   const S* s = (const S*)src;
   S* d = (S*)dst;
+  if constexpr (sizeof(S) == 8) {
+    if (h->cfg.eta_over_s > 0) {
+      k_step<S, false, false, true><<<grid, bx, 0, st>>>(s, d, geo, h->k, h->d_bad);
+      return cudaGetLastError();
+    }
+  }
   if (!mrt) k_step<S, false, false><<<grid, bx, 0, st>>>(s, d, geo, h->k, h->d_bad);
   else if (!q) k_step<S, true, false><<<grid, bx, 0, st>>>(s, d, geo, h->k, h->d_bad);
   else k_step<S, true, true><<<grid, bx, 0, st>>>(s, d, geo, h->k, h->d_bad);
@@ -348,8 +354,15 @@ extern "C" int rlb_create(const rlb_config* cfg, rlb_handle** out) {
     if (cfg->bc[a] != RLB_PERIODIC && cfg->bc[a] != RLB_ZERO_GRADIENT)
       return fail(nullptr, RLB_EINVAL, "unknown boundary type");
   std::string why;
-  if (rlb::validate_taus(cfg->tau_f, cfg->tau_v, cfg->tau_e, cfg->tau_eps, cfg->tau_q, cfg->collision, why))
+  const bool eta_mode = cfg->eta_over_s > 0;
+  if (eta_mode && (cfg->collision != RLB_BGK || cfg->lattice != RLB_D3Q19 || cfg->precision != RLB_FP64))
+    return fail(nullptr, RLB_EINVAL, "eta_over_s needs RLB_BGK, RLB_D3Q19 and RLB_FP64");
+  if (!(cfg->eta_over_s >= 0)) return fail(nullptr, RLB_EINVAL, "eta_over_s must be >= 0");
+  if (!eta_mode &&
+      rlb::validate_taus(cfg->tau_f, cfg->tau_v, cfg->tau_e, cfg->tau_eps, cfg->tau_q, cfg->collision, why))
     return fail(nullptr, RLB_EINVAL, why);
+  if (eta_mode && cfg->tau_f > 0 && !(cfg->tau_f > 0.5))
+    return fail(nullptr, RLB_EINVAL, "tau_f must be > 0.5 (or <= 0 for tau_f = tau_g)");
   const unsigned long long nodes = (unsigned long long)cfg->nx * cfg->ny * cfg->nz;
   if (nodes >= (1ull << 32) || (unsigned long long)cfg->ny * cfg->nz > 65535ull * 65535ull || cfg->ny > 65535 ||
       cfg->nz > 65535)
@@ -361,8 +374,10 @@ extern "C" int rlb_create(const rlb_config* cfg, rlb_handle** out) {
   h->nodes = nodes;
   h->esize = cfg->precision == RLB_FP64 ? 8 : 4;
   h->Q = cfg->lattice == RLB_D2Q9 ? 9 : 19;
-  h->k = make_step_const(cfg->tau_f, cfg->tau_v, cfg->tau_e, cfg->tau_eps, cfg->tau_q, cfg->collision == RLB_MRT,
-                         h->Q);
+  h->k = make_step_const(eta_mode && cfg->tau_f <= 0 ? 1.0 : cfg->tau_f, eta_mode ? 1.0 : cfg->tau_v, cfg->tau_e,
+                         cfg->tau_eps, cfg->tau_q, cfg->collision == RLB_MRT, h->Q);
+  h->k.eta_s = cfg->eta_over_s;
+  h->k.tauf_local = eta_mode && cfg->tau_f <= 0;
   cudaGetDevice(&h->device);
   const size_t bytes = 2 * (size_t)h->Q * h->nodes * h->esize;
   for (int i = 0; i < 2; ++i) {

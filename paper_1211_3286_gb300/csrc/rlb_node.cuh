@@ -67,6 +67,9 @@ struct StepConst {
   float omf_f, omf1_f, fA_k_f, fD_k_f, f0_k_f, fA_s_f, fD_s_f, fA_a_f, fD_a_f;
   float omv_f, omv1_f, gA_k_f, gD_k_f, gA_s_f, gD_s_f, gA_a_f, gD_a_f;
   float ce_f, cp_f, cq_f;
+  // fixed-eta/s relaxation (BGK): eta_s > 0 derives tau_g per node; tauf_local: tau_f = tau_g
+  double eta_s;
+  int tauf_local;
 };
 
 // q = 19 (D3Q19: weights 1/3, 1/18, 1/36; MRT row norms e 2394, eps 252, q 40) or
@@ -240,12 +243,40 @@ __device__ __forceinline__ void pair_cu(C ux, C uy, C uz, C (&cu)[9]) {
 
 // FP64 node collide: moments, recovery, equilibria, BGK f, BGK / MRT g.
 // f and g hold the pulled populations on entry and the post-collision ones on exit.
-template <bool MRT, bool QSEP>
-__device__ __forceinline__ bool node_collide_f64(double (&f)[19], double (&g)[19], const StepConst& k) {
+// Relaxation coefficients of the BGK f and g collisions for given omega_f, omega_v
+// (D3Q19 weights), as make_step_const prepares them for constant taus.
+__device__ __forceinline__ void set_bgk_coefficients(StepConst& k, double omf, double omv) {
+  const double wA = 1.0 / 18.0, wD = 1.0 / 36.0, w0 = 1.0 / 3.0;
+  k.omf = omf; k.omf1 = 1.0 - omf;
+  k.fA_k = omf * wA; k.fD_k = omf * wD; k.f0_k = omf * w0;
+  k.fA_s = 4.5 * omf * wA; k.fD_s = 4.5 * omf * wD; k.fA_a = 3.0 * omf * wA; k.fD_a = 3.0 * omf * wD;
+  k.omv = omv; k.omv1 = 1.0 - omv;
+  k.gA_k = omv * wA; k.gD_k = omv * wD;
+  k.gA_s = 4.5 * omv * wA; k.gD_s = 4.5 * omv * wD; k.gA_a = 3.0 * omv * wA; k.gD_a = 3.0 * omv * wD;
+}
+
+// tau_g from a fixed eta/s (Sec. II and III.B): eta = (tau - 1/2) c_s^2 (e + P) gamma,
+// eta = (eta/s) s, s = n (4 - ln(n / n_eq)), n_eq = d_G T^3 / pi^2 (d_G = 16), T = P / n.
+__device__ __forceinline__ double tau_eta_over_s(double eta_s, const NodeMacro& m) {
+  const double inv_gamma = sqrt(1.0 - m.u2);
+  const double n = m.N0 * inv_gamma;
+  const double T = m.P / n;
+  const double n_eq = (16.0 / (M_PI * M_PI)) * T * T * T;
+  const double s = n * (4.0 - log(n / n_eq));
+  return 0.5 + (eta_s * s) * inv_gamma / ((1.0 / 3.0) * 4.0 * m.P);   // (e + P) = 4 P
+}
+
+template <bool MRT, bool QSEP, bool ETA = false>
+__device__ __forceinline__ bool node_collide_f64(double (&f)[19], double (&g)[19], const StepConst& kc) {
   double sp[9], dp[9], Sa, Sd;
   NodeMacro m;
   node_moments<double>(f, g, sp, dp, Sa, Sd, m);
   node_recover_fast(m);
+  StepConst k = kc;
+  if (ETA) {
+    const double omv = 1.0 / tau_eta_over_s(kc.eta_s, m);
+    set_bgk_coefficients(k, kc.tauf_local ? omv : kc.omf, omv);
+  }
 
   double cu[9];
   pair_cu<double>(m.ux, m.uy, m.uz, cu);

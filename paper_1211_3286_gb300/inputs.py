@@ -62,13 +62,17 @@ def normal(seed, stream, count) -> np.ndarray:
 # ----------------------------------------------------------------------------- shock tube
 # Sec. V.B moderately relativistic shock: P = 5.43 : 0.339 GeV fm^-3, T = 400 : 200 MeV
 MODERATE = dict(P_left=5.43e-3, P_right=0.339e-3, T_left=2.0, T_right=1.0)
+# Sec. III.B state in the paper's lattice units (eta/s runs need the absolute n = P/T):
+# P = 2.495e-7 : 1.023e-7, T = 0.0314 everywhere
+PAPER_LATTICE_UNITS = dict(P_left=2.495e-7, P_right=1.023e-7, T_left=0.0314, T_right=0.0314, absolute_n=True)
 
 
-def shock_tube(L: int, P_left: float = 5.43e-3, P_right: float = 2.22e-3, T_left=None, T_right=None):
+def shock_tube(L: int, P_left: float = 5.43e-3, P_right: float = 2.22e-3, T_left=None, T_right=None,
+               absolute_n: bool = False):
     """Quasi-1D Riemann problem along x on an L x 1 x 1 lattice.  Returns numpy
     arrays e, ux, uy, uz, n of shape (1, 1, L) in (z, y, x) order.  Without
-    temperatures n = (e / e_L)^(3/4); with T_left / T_right, n = P / T normalised to
-    n_L = 1 (the paper's n = P / T of Sec. III.B and V.B)."""
+    temperatures n = (e / e_L)^(3/4); with T_left / T_right, n = P / T (the paper's
+    n = P / T of Sec. III.B and V.B), normalised to n_L = 1 unless absolute_n."""
     i = np.arange(L)
     P = np.where(i < L // 2, P_left, P_right).astype(np.float64)
     e = 3.0 * P
@@ -77,7 +81,7 @@ def shock_tube(L: int, P_left: float = 5.43e-3, P_right: float = 2.22e-3, T_left
         n = (e / eL) ** 0.75
     else:
         Tn = np.where(i < L // 2, T_left, T_right).astype(np.float64)
-        n = (P / Tn) / (P_left / T_left)
+        n = (P / Tn) if absolute_n else (P / Tn) / (P_left / T_left)
     z = np.zeros_like(e)
     sh = (1, 1, L)
     return e.reshape(sh), z.reshape(sh), z.copy().reshape(sh), z.copy().reshape(sh), n.reshape(sh)

@@ -38,7 +38,7 @@ class Lattice:
 
     def __init__(self, shape, collision="mrt", tau_f=0.9, tau_v=0.9, tau_e=0.9, tau_eps=0.9, tau_q=0.0,
                  bc=("periodic", "periodic", "periodic"), precision="fp64", stream=None, lattice="d3q19",
-                 correction=False):
+                 correction=False, eta_over_s=0.0):
         nz, ny, nx = shape
         self.shape = (nz, ny, nx)
         self.precision = precision
@@ -52,6 +52,7 @@ class Lattice:
             cfg.bc[a] = _BC[bc[a]]
         cfg.precision = _PREC[precision]
         cfg.correction = L.RLB_CORR_C7 if correction else L.RLB_CORR_NONE
+        cfg.eta_over_s = eta_over_s
         if stream is None and torch.cuda.is_available():
             stream = torch.cuda.current_stream()
         cfg.stream = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)

@@ -303,3 +303,23 @@ def test_moderately_relativistic_breakdown_flagged_like_the_oracle():
         lat.check()
     assert ex.value.code == L.RLB_ENONPHYS
     lat.close()
+
+
+# ----------------------------------------------------------------------------- eta/s relaxation (Sec. III.B, Fig. 1)
+@pytest.mark.parametrize("eta_s, tau_f", [(0.1, 0.0), (0.1, 0.6), (0.01, 1.0)])
+def test_eta_over_s_relaxation_fig1(eta_s, tau_f):
+    """BGK with tau_g per node from eta/s (the paper's lattice-unit state, n = P/T),
+    tau_f = tau_g (0.0) or constant; 800 nodes, 400 steps; parity with the oracle."""
+    from paper_1211_3286_gb300.lattice import Lattice
+    L, T = 800, 400
+    e, ux, uy, uz, n = (torch.from_numpy(a) for a in I.shock_tube(L, **I.PAPER_LATTICE_UNITS))
+    lat = Lattice((1, 1, L), collision="bgk", tau_f=tau_f, tau_v=0.9, bc=("zero_gradient", "periodic", "periodic"),
+                  eta_over_s=eta_s)
+    lat.set_fields(e.cuda(), ux.cuda(), uy.cuda(), uz.cuda(), n.cuda())
+    lat.step(T)
+    gpu = lat.fields("cuda")
+    lat.close()
+    prm = O.Params(collision="bgk", tau_f=tau_f, eta_over_s=eta_s, bc=(O.ZERO_GRADIENT, O.PERIODIC, O.PERIODIC))
+    ref = oracle_fields(*O.run(*O.init_populations(e, torch.stack([ux, uy, uz]), n), prm, T))
+    err = field_errors(gpu, ref)
+    assert max(err.values()) < TOL64, err

@@ -556,3 +556,36 @@ def test_moderately_relativistic_shock_low_viscosity_is_nonphysical():
     with pytest.raises(O.NonPhysical):
         O.run(*O.init_populations(e, torch.stack([ux, uy, uz]), n), prm, 300)
     del c
+
+
+# ----------------------------------------------------------------------------- eta/s and the tau_f study (Sec. III.B, Fig. 1)
+def test_tau_from_eta_over_s_matches_printed_value():
+    """With the paper's lattice-unit state (P = 2.495e-7 : 1.023e-7, T = 0.0314, n = P/T)
+    and eta/s = 0.1, eta = (tau_g - 1/2) c_s^2 (e + P) gamma with s = 4n - n ln(n/n_eq)
+    gives tau_g = 14.46 (left) and 16.59 (right): 'around 15.5' as printed."""
+    c = _golden_constants()
+    P = torch.tensor([c["P_left_lattice"], c["P_right_lattice"]], dtype=torch.float64)
+    n = P / c["T_lattice"]
+    f, g = O.init_populations(3 * P, torch.zeros(3, 2, dtype=torch.float64), n)
+    tau = O.tau_from_eta_over_s(0.1, O.fields(f, g))
+    assert abs(float(tau.mean()) - c["tau_g_eta_s_0p1"]) < 0.1
+    assert 14.0 < float(tau[0]) < 15.0 and 16.0 < float(tau[1]) < 17.0
+
+
+def test_fig1_number_profile_depends_on_tau_f():
+    """Fig. 1 / Eq. 23: with tau_g from eta/s, tau_f = tau_g smooths the number profile far
+    more than tau_f = 0.6 at eta/s = 0.1, and the gap grows with eta/s."""
+    L, T = 800, 400
+    e, ux, uy, uz, n = (torch.from_numpy(a) for a in I.shock_tube(L, **I.PAPER_LATTICE_UNITS))
+    u = torch.stack([ux, uy, uz])
+
+    def steepest(es, tf):
+        prm = O.Params(collision="bgk", tau_f=tf, eta_over_s=es, bc=(O.ZERO_GRADIENT, O.PERIODIC, O.PERIODIC))
+        fl = O.fields(*O.run(*O.init_populations(e, u, n), prm, T))
+        nn = fl.n.reshape(-1)
+        return float((nn[1:] - nn[:-1]).abs().max() / nn.max())
+
+    r_hi = steepest(0.1, 0.6) / steepest(0.1, 0.0)
+    r_lo = steepest(0.01, 0.6) / steepest(0.01, 0.0)
+    assert r_hi > 3.0 and r_lo < r_hi
+    assert steepest(0.1, 0.0) < steepest(0.1, 1.0) < steepest(0.1, 0.6)
