@@ -87,7 +87,10 @@ extern "C" {
  *            per node and step, tau_g = 1/2 + eta / (c_s^2 (e + P) gamma) with
  *            eta = (eta/s) s, s = 4 n - n ln(n / n_eq), n_eq = 16 T^3 / pi^2 and
  *            T = P / n; tau_v is then unused and tau_f <= 0 means tau_f = tau_g
- *            (the Fig. 1 cases); n must be given in the same units as P.
+ *            (the Fig. 1 cases); n must be given in the same units as P.  With
+ *            RLB_MRT, tau_v = tau_g per node and tau_e, tau_eps, tau_q are read as
+ *            the ratios a_x = (tau_x - 1/2) / (tau_v - 1/2) (Cases A-D of Sec. V.B;
+ *            tau_q <= 0 means 1).
  */
 typedef struct rlb_config {
   int nx, ny, nz;
@@ -99,7 +102,7 @@ typedef struct rlb_config {
   int precision;    /* RLB_FP64 | RLB_FP32_STORAGE */
   void* stream;
   int correction;   /* RLB_CORR_NONE | RLB_CORR_C7 (RLB_D2Q9 + RLB_MRT only, flow along x) */
-  double eta_over_s; /* > 0: per-node tau_g from eta/s (RLB_BGK, RLB_D3Q19, RLB_FP64); 0: constant taus */
+  double eta_over_s; /* > 0: per-node tau_g / tau_v from eta/s (RLB_FP64); 0: constant taus */
 } rlb_config;
 
 typedef struct rlb_handle rlb_handle;

@@ -286,7 +286,9 @@ def relaxation_diag(tau_v, tau_e, tau_eps, tau_q, like=None, lat="d3q19"):
     one = torch.ones((), dtype=tv.dtype)
     rate = {"rho": one, "jx": one, "jy": one, "jz": one,
             "e": 1.0 / te, "eps": 1.0 / tp, "qx": 1.0 / tq, "qy": 1.0 / tq, "qz": 1.0 / tq}
-    return torch.stack([rate.get(name, 1.0 / tv) * one for name in mrt_rows(lat)])
+    rows = [rate.get(name, 1.0 / tv) * one for name in mrt_rows(lat)]
+    shape = torch.broadcast_shapes(*[r.shape for r in rows])      # per-node taus give (Q, nodes)
+    return torch.stack([r.expand(shape) for r in rows])
 
 
 # ----------------------------------------------------------------------------- collision
@@ -304,7 +306,8 @@ def collide_mrt(g, geq, S):
     shape = g.shape
     m = Mx @ g.reshape(Q, -1)
     meq = Mx @ geq.reshape(Q, -1)
-    mstar = m - S.to(g.dtype).reshape(Q, 1) * (m - meq)
+    Sd = S.to(g.dtype)
+    mstar = m - (Sd.reshape(Q, 1) if Sd.dim() == 1 else Sd) * (m - meq)   # S per row, or per row and node
     return (Minv @ mstar).reshape(shape)
 
 
@@ -347,8 +350,10 @@ class Params:
     bc: tuple = (PERIODIC, PERIODIC, PERIODIC)
     lattice: str = "d3q19"               # or "d2q9" (the MRT model of Sec. V.A)
     correction: bool = False             # D2Q9 MRT only: the C_7 term of Eqs. 37-38 (flow along x)
-    eta_over_s: float = 0.0              # > 0: BGK tau_g per node from eta/s (Sec. II, III.B); tau_v unused
-                                         # then, and tau_f <= 0 means tau_f = tau_g
+    eta_over_s: float = 0.0              # > 0: tau_g (BGK) or tau_v (MRT) per node from eta/s (Sec. II,
+                                         # III.B); tau_f <= 0 then means tau_f = tau_g; for MRT tau_e,
+                                         # tau_eps, tau_q are read as the ratios (tau_x - 1/2)/(tau_v - 1/2)
+                                         # (the a of Cases B-D, Sec. V.B)
 
     def tq(self):
         return self.tau_v if (not torch.is_tensor(self.tau_q) and self.tau_q <= 0) else self.tau_q
@@ -367,11 +372,16 @@ def collide(f, g, prm: Params, check: bool = True):
     feq = f_eq(fl.n, fl.u, prm.lattice)
     geq = g_eq(fl.e, fl.P, fl.u, prm.lattice)
     if prm.eta_over_s > 0:
-        if prm.collision != "bgk":
-            raise ValueError("eta/s-derived relaxation times are implemented for the BGK model")
         tg = tau_from_eta_over_s(prm.eta_over_s, fl)
         tf = tg if (not torch.is_tensor(prm.tau_f) and prm.tau_f <= 0) else prm.tau_f
-        return collide_bgk(f, feq, tf), collide_bgk(g, geq, tg)
+        if prm.collision == "bgk":
+            return collide_bgk(f, feq, tf), collide_bgk(g, geq, tg)
+        # MRT: tau_v = tau_g per node; tau_x - 1/2 = a_x (tau_v - 1/2) for e, eps, q
+        aq = prm.tau_q if prm.tau_q > 0 else 1.0
+        S = relaxation_diag(tg.reshape(-1), 0.5 + prm.tau_e * (tg.reshape(-1) - 0.5),
+                            0.5 + prm.tau_eps * (tg.reshape(-1) - 0.5), 0.5 + aq * (tg.reshape(-1) - 0.5),
+                            lat=prm.lattice)
+        return collide_bgk(f, feq, tf), collide_mrt(g, geq, S)
     fs = collide_bgk(f, feq, prm.tau_f)
     if prm.collision == "bgk":
         gs = collide_bgk(g, geq, prm.tau_v)

@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(kBlockX) k_macro_d2q9(const double* __restrict
 
 // D2Q9 (FP64): node (x, y) pulls link a from (x - c_x, y - c_y).  With CORR the
 // C_7 term of Eqs. 37-38 is added to the m_7 = p_xx moment of the result.
-template <bool MRT, bool QSEP, bool CORR>
+template <bool MRT, bool QSEP, bool CORR, bool ETA = false>
 __global__ void __launch_bounds__(kBlockX) k_step_d2q9(const double* __restrict__ src, double* __restrict__ dst,
                                                        Geo geo, StepConst k, unsigned long long* __restrict__ bad,
                                                        const double* __restrict__ q) {
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(kBlockX) k_step_d2q9(const double* __restrict_
   double f[9], g[9];
   const unsigned node = pull_d2q9(src, geo, x, y, f, g);
   NodeMacro m;
-  const bool b = node_collide_d2q9_f64<MRT, QSEP>(f, g, k, m);
+  const bool b = node_collide_d2q9_f64<MRT, QSEP, ETA>(f, g, k, m);
   if (b) atomicMin(bad, (unsigned long long)node);
   if (CORR) {
     // neighbours along x: a zero-gradient end reuses the edge node, a periodic axis wraps
@@ -235,7 +235,10 @@ Geo make_geo(const rlb_handle* h) {
   return g;
 }
 
-bool qsep(const rlb_config& c) { return c.collision == RLB_MRT && c.tau_q > 0 && c.tau_q != c.tau_v; }
+bool qsep(const rlb_config& c) {
+  if (c.eta_over_s > 0) return c.collision == RLB_MRT && c.tau_q > 0 && c.tau_q != 1.0;   // tau_q is a ratio
+  return c.collision == RLB_MRT && c.tau_q > 0 && c.tau_q != c.tau_v;
+}
 
 template <typename S>
 cudaError_t launch_step(rlb_handle* h, const void* src, void* dst, cudaStream_t st) {
@@ -246,7 +249,11 @@ cudaError_t launch_step(rlb_handle* h, const void* src, void* dst, cudaStream_t 
     const bool mrt2 = h->cfg.collision == RLB_MRT, q2 = qsep(h->cfg);
     const double* s2 = (const double*)src;
     double* d2 = (double*)dst;
-    if (h->cfg.correction == RLB_CORR_C7) {
+    if (h->cfg.eta_over_s > 0) {
+      if (!mrt2) k_step_d2q9<false, false, false, true><<<grid2, bx, 0, st>>>(s2, d2, geo, h->k, h->d_bad, nullptr);
+      else if (!q2) k_step_d2q9<true, false, false, true><<<grid2, bx, 0, st>>>(s2, d2, geo, h->k, h->d_bad, nullptr);
+      else k_step_d2q9<true, true, false, true><<<grid2, bx, 0, st>>>(s2, d2, geo, h->k, h->d_bad, nullptr);
+    } else if (h->cfg.correction == RLB_CORR_C7) {
       k_macro_d2q9<<<grid2, bx, 0, st>>>(s2, h->d_macro, geo);
       if (!q2) k_step_d2q9<true, false, true><<<grid2, bx, 0, st>>>(s2, d2, geo, h->k, h->d_bad, h->d_macro);
       else k_step_d2q9<true, true, true><<<grid2, bx, 0, st>>>(s2, d2, geo, h->k, h->d_bad, h->d_macro);
@@ -269,7 +276,9 @@ cudaError_t launch_step(rlb_handle* h, const void* src, void* dst, cudaStream_t 
   S* d = (S*)dst;
   if constexpr (sizeof(S) == 8) {
     if (h->cfg.eta_over_s > 0) {
-      k_step<S, false, false, true><<<grid, bx, 0, st>>>(s, d, geo, h->k, h->d_bad);
+      if (!mrt) k_step<S, false, false, true><<<grid, bx, 0, st>>>(s, d, geo, h->k, h->d_bad);
+      else if (!q) k_step<S, true, false, true><<<grid, bx, 0, st>>>(s, d, geo, h->k, h->d_bad);
+      else k_step<S, true, true, true><<<grid, bx, 0, st>>>(s, d, geo, h->k, h->d_bad);
       return cudaGetLastError();
     }
   }
@@ -355,8 +364,10 @@ extern "C" int rlb_create(const rlb_config* cfg, rlb_handle** out) {
       return fail(nullptr, RLB_EINVAL, "unknown boundary type");
   std::string why;
   const bool eta_mode = cfg->eta_over_s > 0;
-  if (eta_mode && (cfg->collision != RLB_BGK || cfg->lattice != RLB_D3Q19 || cfg->precision != RLB_FP64))
-    return fail(nullptr, RLB_EINVAL, "eta_over_s needs RLB_BGK, RLB_D3Q19 and RLB_FP64");
+  if (eta_mode && (cfg->precision != RLB_FP64 || cfg->correction != RLB_CORR_NONE))
+    return fail(nullptr, RLB_EINVAL, "eta_over_s needs RLB_FP64 and no correction term");
+  if (eta_mode && cfg->collision == RLB_MRT && (!(cfg->tau_e > 0) || !(cfg->tau_eps > 0)))
+    return fail(nullptr, RLB_EINVAL, "eta_over_s with RLB_MRT reads tau_e, tau_eps (and tau_q > 0) as ratios > 0");
   if (!(cfg->eta_over_s >= 0)) return fail(nullptr, RLB_EINVAL, "eta_over_s must be >= 0");
   if (!eta_mode &&
       rlb::validate_taus(cfg->tau_f, cfg->tau_v, cfg->tau_e, cfg->tau_eps, cfg->tau_q, cfg->collision, why))
@@ -378,6 +389,9 @@ extern "C" int rlb_create(const rlb_config* cfg, rlb_handle** out) {
                          cfg->tau_eps, cfg->tau_q, cfg->collision == RLB_MRT, h->Q);
   h->k.eta_s = cfg->eta_over_s;
   h->k.tauf_local = eta_mode && cfg->tau_f <= 0;
+  h->k.a_e = cfg->tau_e;
+  h->k.a_p = cfg->tau_eps;
+  h->k.a_q = cfg->tau_q > 0 ? cfg->tau_q : 1.0;
   cudaGetDevice(&h->device);
   const size_t bytes = 2 * (size_t)h->Q * h->nodes * h->esize;
   for (int i = 0; i < 2; ++i) {

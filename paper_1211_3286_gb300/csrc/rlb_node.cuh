@@ -67,9 +67,11 @@ struct StepConst {
   float omf_f, omf1_f, fA_k_f, fD_k_f, f0_k_f, fA_s_f, fD_s_f, fA_a_f, fD_a_f;
   float omv_f, omv1_f, gA_k_f, gD_k_f, gA_s_f, gD_s_f, gA_a_f, gD_a_f;
   float ce_f, cp_f, cq_f;
-  // fixed-eta/s relaxation (BGK): eta_s > 0 derives tau_g per node; tauf_local: tau_f = tau_g
+  // fixed-eta/s relaxation: eta_s > 0 derives tau_g (BGK) / tau_v (MRT) per node; tauf_local:
+  // tau_f = tau_g; for MRT the ratios a_x = (tau_x - 1/2) / (tau_v - 1/2) of e, eps, q
   double eta_s;
   int tauf_local;
+  double a_e, a_p, a_q;
 };
 
 // q = 19 (D3Q19: weights 1/3, 1/18, 1/36; MRT row norms e 2394, eps 252, q 40) or
@@ -255,6 +257,16 @@ __device__ __forceinline__ void set_bgk_coefficients(StepConst& k, double omf, d
   k.gA_s = 4.5 * omv * wA; k.gD_s = 4.5 * omv * wD; k.gA_a = 3.0 * omv * wA; k.gD_a = 3.0 * omv * wD;
 }
 
+// Per-node MRT rates of the fixed-eta/s mode: tau_x = 1/2 + a_x (tau_v - 1/2) for e, eps, q;
+// q = 19 or 9 selects the row norms.
+__device__ __forceinline__ void set_mrt_eta_coefficients(StepConst& k, double tau_v, int q) {
+  const bool d2 = q == 9;
+  const double h = tau_v - 0.5;
+  k.ce = (1.0 / fma(k.a_e, h, 0.5) - k.omv) * (d2 ? 1.0 / 36.0 : 1.0 / 2394.0);
+  k.cp = (1.0 / fma(k.a_p, h, 0.5) - k.omv) * (d2 ? 1.0 / 36.0 : 1.0 / 252.0);
+  k.cq = (1.0 / fma(k.a_q, h, 0.5) - k.omv) * (d2 ? 1.0 / 12.0 : 1.0 / 40.0);
+}
+
 // tau_g from a fixed eta/s (Sec. II and III.B): eta = (tau - 1/2) c_s^2 (e + P) gamma,
 // eta = (eta/s) s, s = n (4 - ln(n / n_eq)), n_eq = d_G T^3 / pi^2 (d_G = 16), T = P / n.
 __device__ __forceinline__ double tau_eta_over_s(double eta_s, const NodeMacro& m) {
@@ -274,8 +286,10 @@ __device__ __forceinline__ bool node_collide_f64(double (&f)[19], double (&g)[19
   node_recover_fast(m);
   StepConst k = kc;
   if (ETA) {
-    const double omv = 1.0 / tau_eta_over_s(kc.eta_s, m);
+    const double tv = tau_eta_over_s(kc.eta_s, m);
+    const double omv = 1.0 / tv;
     set_bgk_coefficients(k, kc.tauf_local ? omv : kc.omf, omv);
+    if (MRT) set_mrt_eta_coefficients(k, tv, 19);
   }
 
   double cu[9];
@@ -647,12 +661,30 @@ __device__ __forceinline__ void node_moments_d2q9(const S (&f)[9], const S (&g)[
                          (((double)f[5] + (double)f[6]) + ((double)f[7] + (double)f[8])));
 }
 
-template <bool MRT, bool QSEP>
-__device__ __forceinline__ bool node_collide_d2q9_f64(double (&f)[9], double (&g)[9], const StepConst& k,
+// D2Q9 relaxation coefficients for given omega_f, omega_v (weights 4/9, 1/9, 1/36).
+__device__ __forceinline__ void set_bgk_coefficients_d2q9(StepConst& k, double omf, double omv) {
+  const double wA = 1.0 / 9.0, wD = 1.0 / 36.0, w0 = 4.0 / 9.0;
+  k.omf = omf; k.omf1 = 1.0 - omf;
+  k.fA_k = omf * wA; k.fD_k = omf * wD; k.f0_k = omf * w0;
+  k.fA_s = 4.5 * omf * wA; k.fD_s = 4.5 * omf * wD; k.fA_a = 3.0 * omf * wA; k.fD_a = 3.0 * omf * wD;
+  k.omv = omv; k.omv1 = 1.0 - omv;
+  k.gA_k = omv * wA; k.gD_k = omv * wD;
+  k.gA_s = 4.5 * omv * wA; k.gD_s = 4.5 * omv * wD; k.gA_a = 3.0 * omv * wA; k.gD_a = 3.0 * omv * wD;
+}
+
+template <bool MRT, bool QSEP, bool ETA = false>
+__device__ __forceinline__ bool node_collide_d2q9_f64(double (&f)[9], double (&g)[9], const StepConst& kc,
                                                       NodeMacro& m) {
   double dp[4], Sa, Sd;
   node_moments_d2q9<double>(f, g, dp, Sa, Sd, m);
   node_recover_fast(m);
+  StepConst k = kc;
+  if (ETA) {
+    const double tv = tau_eta_over_s(kc.eta_s, m);
+    const double omv = 1.0 / tv;
+    set_bgk_coefficients_d2q9(k, kc.tauf_local ? omv : kc.omf, omv);
+    if (MRT) set_mrt_eta_coefficients(k, tv, 9);
+  }
   double cu[4];
   cu[0] = m.ux; cu[1] = m.uy; cu[2] = m.ux + m.uy; cu[3] = m.ux - m.uy;
   {

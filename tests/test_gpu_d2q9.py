@@ -124,3 +124,47 @@ def test_c7_rejected_outside_d2q9_mrt():
         Lattice((1, 4, 8), lattice="d3q19", correction=True)
     with pytest.raises(L.RlbError):
         Lattice((1, 4, 8), lattice="d2q9", collision="bgk", correction=True)
+
+
+@pytest.mark.parametrize("case", ["A", "B", "C", "D"])
+def test_d2q9_cases_with_eta_over_s(case):
+    """Sec. V.B with tau_v per node from eta/s = 0.5 (paper's lattice-unit state, 4 x 800,
+    400 steps), Cases A-D as ratios a_x = (tau_x - 1/2)/(tau_v - 1/2): parity with the oracle."""
+    from paper_1211_3286_gb300.lattice import Lattice
+    a = 1.0 / 20.0
+    ratios = {"A": (1, 1, 1), "B": (1, 1, a), "C": (a, 1, 1), "D": (a, a, 1)}[case]
+    L, T = 800, 400
+    e, ux, uy, uz, n = (torch.from_numpy(x) for x in I.shock_tube(L, **I.PAPER_LATTICE_UNITS))
+    e2, n2 = e.expand(1, 4, L).contiguous(), n.expand(1, 4, L).contiguous()
+    z = torch.zeros_like(e2)
+    bc = ("zero_gradient", "periodic", "periodic")
+    lat = Lattice((1, 4, L), collision="mrt", tau_f=0.0, tau_v=0.9, tau_e=ratios[0], tau_eps=ratios[1],
+                  tau_q=ratios[2], bc=bc, lattice="d2q9", eta_over_s=0.5)
+    lat.set_fields(e2.cuda(), z.cuda(), z.cuda(), z.cuda(), n2.cuda())
+    lat.step(T)
+    gpu = lat.fields("cuda")
+    lat.close()
+    prm = O.Params(collision="mrt", tau_f=0.0, tau_e=ratios[0], tau_eps=ratios[1], tau_q=ratios[2], eta_over_s=0.5,
+                   lattice="d2q9", bc=oracle_bc(bc))
+    ref = oracle_fields(*O.run(*O.init_populations(e2, torch.stack([z, z, z]), n2, "d2q9"), prm, T))
+    err = field_errors(gpu, ref)
+    assert max(err.values()) < TOL64, err
+    c = L // 2
+    jump = float((gpu["ux"][0, 0, c] - gpu["ux"][0, 0, c - 1]).abs())
+    assert (jump > 1e-2) if case in "AB" else (jump < 1e-3)
+
+
+def test_d3q19_mrt_with_eta_over_s():
+    from paper_1211_3286_gb300.lattice import Lattice
+    L, T = 400, 300
+    e, ux, uy, uz, n = (torch.from_numpy(x) for x in I.shock_tube(L, **I.PAPER_LATTICE_UNITS))
+    bc = ("zero_gradient", "periodic", "periodic")
+    lat = Lattice((1, 1, L), collision="mrt", tau_f=0.6, tau_v=0.9, tau_e=0.05, tau_eps=0.05, tau_q=0.5, bc=bc,
+                  eta_over_s=0.2)
+    lat.set_fields(e.cuda(), ux.cuda(), uy.cuda(), uz.cuda(), n.cuda())
+    lat.step(T)
+    gpu = lat.fields("cuda")
+    lat.close()
+    prm = O.Params(collision="mrt", tau_f=0.6, tau_e=0.05, tau_eps=0.05, tau_q=0.5, eta_over_s=0.2, bc=oracle_bc(bc))
+    ref = oracle_fields(*O.run(*O.init_populations(e, torch.stack([ux, uy, uz]), n), prm, T))
+    assert max(field_errors(gpu, ref).values()) < TOL64

@@ -224,3 +224,30 @@ def test_c7_only_changes_m7_and_keeps_conservation():
     t1 = O.conserved_totals(fr, gr)
     scale = torch.tensor([t0[0], t0[1], t0[1], t0[1], t0[1]])
     assert ((t1 - t0).abs() / scale).max() < 1e-13
+
+
+# ----------------------------------------------------------------------------- Sec. V.B cases A-D with eta/s
+def test_membrane_discontinuity_cases_a_to_d():
+    """Sec. V.B, Figs. 2-5: with tau_v from eta/s (paper's lattice-unit state, 4 x 800,
+    t = 400), Cases A and B leave a velocity jump at the membrane that is the steepest
+    point of the profile and grows with eta/s; tau_q (Case B) changes nothing visible;
+    Cases C and D (tau_e - 1/2 = a (tau_v - 1/2), a = 1/20) remove it."""
+    L, T, a = 800, 400, 1.0 / 20.0
+    e, ux, uy, uz, n = (torch.from_numpy(x) for x in I.shock_tube(L, **I.PAPER_LATTICE_UNITS))
+    e2, n2 = e.expand(1, 4, L).contiguous(), n.expand(1, 4, L).contiguous()
+    u2 = torch.zeros(3, 1, 4, L, dtype=torch.float64)
+
+    def profile(es, ae, ap, aq):
+        prm = O.Params(collision="mrt", tau_f=0.0, tau_e=ae, tau_eps=ap, tau_q=aq, eta_over_s=es, lattice="d2q9",
+                       bc=ZG)
+        return O.fields(*O.run(*O.init_populations(e2, u2, n2, "d2q9"), prm, T)).u[0, 0, 0]
+
+    c = L // 2
+    A5, B5, D5, A2 = profile(0.5, 1, 1, 1), profile(0.5, 1, 1, a), profile(0.5, a, a, 1), profile(0.2, 1, 1, 1)
+    jump = lambda u: float((u[c] - u[c - 1]).abs())
+    steepest = lambda u: int((u[1:] - u[:-1]).abs().argmax()) + 1
+    assert steepest(A5) == c and steepest(A2) == c
+    assert jump(A5) > 5 * jump(A2)
+    assert float((A5 - B5).abs().max()) < 1e-3 * jump(A5)
+    assert jump(D5) < jump(A5) / 50
+    assert steepest(D5) != c
