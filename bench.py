@@ -63,13 +63,14 @@ TAUS = dict(tau_f=0.9, tau_v=0.9, tau_e=0.55, tau_eps=0.8)
 # the integer sums + equilibrium constants 5.
 FP64_OPS_PER_UPDATE_F32S = 27
 
-# FP64 flops (FMA = 2, sqrt and division = 1) of one FP64 MRT node update,
-# counted from the per-node arithmetic of the step kernel: moments 57,
-# recovery 23, f relaxation 102 (+6 pair velocities), g relaxation 97, MRT 27.
-FLOPS_PER_UPDATE_F64 = 312
-# The same per-node arithmetic counted as FP64 operations (FMA = 1): moments 57,
-# recovery 17, pair velocities 6, f relaxation 73, g relaxation 87 (MRT 20 of it).
-FP64_OPS_PER_UPDATE = 240
+# FP64 flops (FMA = 2, sqrt and division = 1) of one FP64 MRT node update on the
+# FP64 pipe: recovery 23, f relaxation 102 (+6 pair velocities), g relaxation 97,
+# MRT 27 (the moment sums run exactly on the integer pipe).
+FLOPS_PER_UPDATE_F64 = 255
+# FP64 operations (FMA = 1) the step performs on the FP64 pipe: recovery 17, pair
+# velocities 6, f relaxation 73, g relaxation 87 (MRT 20 of it).  The moments of
+# Eq. 10 are exact integer sums on the integer pipe and are not counted.
+FP64_OPS_PER_UPDATE = 183
 
 
 def _dist():

@@ -79,7 +79,7 @@ __device__ __forceinline__ void pull19(const S* __restrict__ base, unsigned long
 }
 
 template <typename S, bool MRT, bool QSEP, bool ETA = false>
-__global__ void __launch_bounds__(kBlockX) k_step(const S* __restrict__ src, S* __restrict__ dst, Geo geo,
+__global__ void __launch_bounds__(kBlockX, sizeof(S) == 8 ? 3 : 1) k_step(const S* __restrict__ src, S* __restrict__ dst, Geo geo,
                                                   StepConst k, unsigned long long* __restrict__ bad) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= geo.nx) return;

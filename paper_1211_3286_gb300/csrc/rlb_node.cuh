@@ -245,6 +245,76 @@ __device__ __forceinline__ void pair_cu(C ux, C uy, C uz, C (&cu)[9]) {
 
 // FP64 node collide: moments, recovery, equilibria, BGK f, BGK / MRT g.
 // f and g hold the pulled populations on entry and the post-collision ones on exit.
+// x * 2^e for a normal double whose scaled value stays normal (exponent add on the
+// bits); zero stays zero
+__device__ __forceinline__ double scale_pow2(double x, int e) {
+  const int hi = __double2hiint(x), lo = __double2loint(x);
+  const bool zero = ((hi & 0x7fffffff) | lo) == 0;
+  return __hiloint2double(zero ? hi : hi + (e << 20), lo);
+}
+
+// ---------------------------------------------------------------------------
+// Exact moment sums of FP64 populations on the integer pipe.
+//
+// Each of the 19 values of a distribution becomes a 64-bit fixed-point integer
+// on the grid of its largest exponent E: its 53-bit significand shifted left by 5
+// (headroom for 19 terms) and right by E - e.  Signed sums of these integers are
+// exact; they equal the true sums except for bits below 2^(E-1080) (below 2^-57 of
+// the largest value), and each is rounded once to FP64.  This takes the ~57 FP64
+// additions of the moments (Eq. 10) off GB300's FP64 pipe (2 instructions per
+// clock per SM) onto the integer pipe.
+__device__ __forceinline__ int max_exp19_f64(const double (&p)[19]) {
+  int E = ((unsigned)__double2hiint(p[0]) >> 20) & 0x7ff;
+#pragma unroll
+  for (int a = 1; a < 19; ++a) E = max(E, (int)(((unsigned)__double2hiint(p[a]) >> 20) & 0x7ffu));
+  return E;
+}
+__device__ __forceinline__ long long fixed_from_f64(double x, int E) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const int ex = (int)((hi >> 20) & 0x7ffu);
+  const unsigned mhi = ex ? ((hi & 0xfffffu) | 0x100000u) : (hi & 0xfffffu);
+  const int sh = min(E - (ex ? ex : 1), 63);
+  const unsigned long long v = ((((unsigned long long)mhi << 32) | lo) << 5) >> sh;
+  return (hi >> 31) ? -(long long)v : (long long)v;
+}
+struct ExactSums64 {
+  long long T00, Mx, My, Mz, Sa, Sd, qx, qy, qz;
+};
+template <bool QSEP>
+__device__ __forceinline__ void exact_sums_g64(const double (&g)[19], int E, ExactSums64& S) {
+  // integer sums are exact in any order: accumulate pair by pair as the values are formed
+  constexpr int cx[9] = {1, 0, 0, 1, 1, 1, 1, 0, 0};
+  constexpr int cy[9] = {0, 1, 0, 1, -1, 0, 0, 1, 1};
+  constexpr int cz[9] = {0, 0, 1, 0, 0, 1, -1, 1, -1};
+  S.Sa = 0; S.Sd = 0; S.Mx = 0; S.My = 0; S.Mz = 0; S.qx = 0; S.qy = 0; S.qz = 0;
+#pragma unroll
+  for (int p = 0; p < 9; ++p) {
+    const long long va = fixed_from_f64(g[2 * p + 1], E), vb = fixed_from_f64(g[2 * p + 2], E);
+    const long long sp = va + vb, dp = va - vb;
+    if (p < 3) S.Sa += sp; else S.Sd += sp;
+    if (cx[p] == 1) S.Mx += dp;
+    if (cy[p] == 1) S.My += dp; else if (cy[p] == -1) S.My -= dp;
+    if (cz[p] == 1) S.Mz += dp; else if (cz[p] == -1) S.Mz -= dp;
+    if (QSEP) {   // q_i = (5|c|^2 - 9) c_i: axis weight -4, diagonal +1
+      const long long w = p < 3 ? -4 : 1;
+      if (cx[p] == 1) S.qx += w * dp;
+      if (cy[p] == 1) S.qy += w * dp; else if (cy[p] == -1) S.qy -= w * dp;
+      if (cz[p] == 1) S.qz += w * dp; else if (cz[p] == -1) S.qz -= w * dp;
+    }
+  }
+  S.T00 = fixed_from_f64(g[0], E) + S.Sa + S.Sd;
+}
+__device__ __forceinline__ long long exact_sum_f64(const double (&f)[19], int E) {
+  long long s = 0;
+#pragma unroll
+  for (int a = 0; a < 19; ++a) s += fixed_from_f64(f[a], E);
+  return s;
+}
+// K * 2^(E - 1080) as the nearest double (one rounding, exponent set by integer add)
+__device__ __forceinline__ double fixed_to_f64(long long K, int E) {
+  return scale_pow2(__ll2double_rn(K), E - 1080);
+}
+
 // Relaxation coefficients of the BGK f and g collisions for given omega_f, omega_v
 // (D3Q19 weights), as make_step_const prepares them for constant taus.
 __device__ __forceinline__ void set_bgk_coefficients(StepConst& k, double omf, double omv) {
@@ -280,10 +350,19 @@ __device__ __forceinline__ double tau_eta_over_s(double eta_s, const NodeMacro& 
 
 template <bool MRT, bool QSEP, bool ETA = false>
 __device__ __forceinline__ bool node_collide_f64(double (&f)[19], double (&g)[19], const StepConst& kc) {
-  double sp[9], dp[9], Sa, Sd;
   NodeMacro m;
-  node_moments<double>(f, g, sp, dp, Sa, Sd, m);
+  const int Eg = max_exp19_f64(g), Ef = max_exp19_f64(f);
+  ExactSums64 X;
+  exact_sums_g64<QSEP>(g, Eg, X);
+  m.T00 = fixed_to_f64(X.T00, Eg);
+  m.Mx = fixed_to_f64(X.Mx, Eg);
+  m.My = fixed_to_f64(X.My, Eg);
+  m.Mz = fixed_to_f64(X.Mz, Eg);
+  m.N0 = fixed_to_f64(exact_sum_f64(f, Ef), Ef);
+  const double Sa = MRT ? fixed_to_f64(X.Sa, Eg) : 0.0;
+  const double Sd = MRT ? fixed_to_f64(X.Sd, Eg) : 0.0;
   node_recover_fast(m);
+  m.bad |= (Eg == 0x7ff) || (Ef == 0x7ff);
   StepConst k = kc;
   if (ETA) {
     const double tv = tau_eta_over_s(kc.eta_s, m);
@@ -338,9 +417,9 @@ __device__ __forceinline__ bool node_collide_f64(double (&f)[19], double (&g)[19
       if (QSEP) {
         // energy-flux rows q_i = (5|c|^2 - 9) c_i: axis weight -4, diagonal +1
         const double qeq = -2.0 / 3.0;
-        const double qx = fma(-4.0, dp[0], ((dp[3] + dp[4]) + dp[5]) + dp[6]);
-        const double qy = fma(-4.0, dp[1], ((dp[3] - dp[4]) + dp[7]) + dp[8]);
-        const double qz = fma(-4.0, dp[2], ((dp[5] - dp[6]) + dp[7]) - dp[8]);
+        const double qx = fixed_to_f64(X.qx, Eg);
+        const double qy = fixed_to_f64(X.qy, Eg);
+        const double qz = fixed_to_f64(X.qz, Eg);
         const double aqx = k.cq * fma(-qeq, m.Mx, qx);
         const double aqy = k.cq * fma(-qeq, m.My, qy);
         const double aqz = k.cq * fma(-qeq, m.Mz, qz);
@@ -475,13 +554,6 @@ __device__ __forceinline__ long long level_int(float v, int eg) {
 }
 __device__ __forceinline__ long long levels_to_int(const float (&v)[3], int E) {
   return (level_int(v[0], E - 18) << 38) + (level_int(v[1], E - 37) << 19) + level_int(v[2], E - 56);
-}
-// x * 2^e for a normal double whose scaled value stays normal (exponent add on the
-// bits); zero stays zero
-__device__ __forceinline__ double scale_pow2(double x, int e) {
-  const int hi = __double2hiint(x), lo = __double2loint(x);
-  const bool zero = ((hi & 0x7fffffff) | lo) == 0;
-  return __hiloint2double(zero ? hi : hi + (e << 20), lo);
 }
 
 // FP32-storage node collide: the conserved sums exact (above) and delivered in
