@@ -245,6 +245,24 @@ def run_tubes(args, dist, rank, ws, local):
                "h2d_bytes_per_step": 5 * nodes * 8 / args.steps, "d2h_bytes_per_step": 6 * nodes * 8 / args.steps,
                "what": "rlb_batch_set_fields(host) + rlb_batch_run(K) + rlb_batch_get_fields(host), pinned"}
     b.close()
+    # shock-tube profile error of the FP32-storage sweep against the FP64 path (same
+    # tubes, taus and steps; outside the timed region)
+    err = None
+    if not args.no_error:
+        out = {}
+        for prec in ("fp32", "fp64"):
+            bb = TubeBatch(lengths, taus, precision=prec, stream=stream)
+            bb.set_fields(*[t.cuda() for t in fields])
+            bb.run(args.steps)
+            bb.check()
+            out[prec] = bb.fields("cuda")
+            bb.close()
+        umax = max(float(out["fp64"][k].abs().max()) for k in ("ux", "uy", "uz"))
+        err = {"per_field": {k: float((out["fp32"][k] - out["fp64"][k]).abs().max())
+                             / (max(umax, 0.1) if k.startswith("u") else float(out["fp64"][k].abs().max()))
+                             for k in ("e", "P", "n", "ux")},
+               "steps": args.steps, "metric": "max|fp32 - fp64| / max|fp64| over all tubes per field, "
+               "velocity over max(max|u|, 0.1); FP64 path = oracle to 1e-12"}
     hbm_peak, peak_kind = _peaks()
     upd_s = nodes * args.steps / (ms / 1e3)
     gbs = 304 * upd_s / 1e9
@@ -265,6 +283,8 @@ def run_tubes(args, dist, rank, ws, local):
                            "ctas_per_sm": shape[1]}, "l2": "batch lattices %.0f MB; one launch covers all steps"
                            % (2 * 38 * nodes * 4 / 1e6)},
                 "roofline": roof, "hbm_roofline": hbm, "clocks": clocks, "e2e": e2e, "gpu_launches": 1}
+        if err is not None:
+            line["error_vs_fp64"] = err
         print(json.dumps(line))
 
 
@@ -378,6 +398,12 @@ def run_ours(args):
                "what": "rlb_set_fields(host) + rlb_step(K) + rlb_get_fields(host), pinned buffers"}
     lat.close()
 
+    # FP32 storage: per-field error of the final fields against the FP64 path on the
+    # same initial fields and step count (outside the timed region)
+    err = None
+    if wl["precision"] == "fp32" and not args.no_error:
+        err = fp32_error_vs_fp64(N, args.steps, stream)
+
     hbm_peak, peak_kind = _peaks()
     gbs = wl["bytes_per_update"] * nodes / per_launch_s / 1e9
     hbm = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
@@ -403,9 +429,38 @@ def run_ours(args):
                            "parallelism": "replicas" if ws > 1 else "single"},
                 "roofline": roof, "hbm_roofline": hbm, "clocks": clocks, "e2e": e2e,
                 "gpu_launches": args.steps}
+        if err is not None:
+            line["error_vs_fp64"] = err
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline(args.ref_seconds)
         print(json.dumps(line))
+
+
+def fp32_error_vs_fp64(N, steps, stream):
+    """Final fields of the FP32-storage lattice against the FP64 lattice (which matches
+    the FP64 oracle to 1e-12) after the same steps from the same initial fields:
+    max|a - b| / max|b| per field, velocities over max(max|u|, 0.1)."""
+    from paper_1211_3286_gb300 import inputs as I
+    from paper_1211_3286_gb300.lattice import Lattice
+    out = {}
+    for prec in ("fp32", "fp64"):
+        with torch.cuda.stream(stream):
+            lat = Lattice((N, N, N), collision="mrt", precision=prec, stream=stream, **TAUS)
+        lat.set_fields(*I.periodic_box(N, device="cuda"))
+        lat.step(steps)
+        lat.check()
+        out[prec] = lat.fields("cuda")
+        lat.close()
+    a, b = out["fp32"], out["fp64"]
+    umax = max(float(b[k].abs().max()) for k in ("ux", "uy", "uz"))
+    err = {}
+    for k in ("e", "P", "n", "ux", "uy", "uz"):
+        scale = max(umax, 0.1) if k.startswith("u") else float(b[k].abs().max())
+        err[k] = float((a[k] - b[k]).abs().max()) / scale
+    del out, a, b
+    torch.cuda.empty_cache()
+    return {"per_field": err, "steps": steps, "metric": "max|fp32 - fp64| / max|fp64| per field, "
+            "velocities over max(max|u|, 0.1); FP64 path = oracle to 1e-12"}
 
 
 def main():
@@ -417,6 +472,8 @@ def main():
     ap.add_argument("--workload", default="box256", choices=sorted(WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-error", action="store_true",
+                    help="skip the FP32-storage error run against the FP64 path")
     ap.add_argument("--ref-seconds", type=float, default=20.0,
                     help="CPU budget of the oracle sample (reference arm and cpu_baseline)")
     args = ap.parse_args()

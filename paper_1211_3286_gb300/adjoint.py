@@ -14,7 +14,7 @@ import ctypes
 import torch
 
 from . import _lib as L
-from .lattice import Lattice, _f64, _ptr
+from .lattice import Lattice, _after_producer, _f64, _ptr
 
 
 def misfit_gradient(lat: Lattice, nsteps, target_P, target_ux, target_uy, target_uz, w_P=1.0, w_u=1.0,
@@ -24,6 +24,7 @@ def misfit_gradient(lat: Lattice, nsteps, target_P, target_ux, target_uy, target
     ts = [_f64(t) for t in (target_P, target_ux, target_uy, target_uz)]
     where = L.RLB_DEVICE if ts[0].is_cuda else L.RLB_HOST
     de0 = torch.empty(lat.shape, dtype=torch.float64, device=ts[0].device)
+    _after_producer(lat.stream, ts + [de0])
     loss, dtau = L.rlb_adjoint(lat.handle, nsteps, checkpoint_every, *[_ptr(t) for t in ts], w_P, w_u, where,
                                _ptr(de0))
     return loss, torch.tensor(dtau, dtype=torch.float64), de0

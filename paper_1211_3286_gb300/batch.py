@@ -7,7 +7,7 @@ import numpy as np
 import torch
 
 from . import _lib as L
-from .lattice import _f64, _ptr, _where
+from .lattice import _after_producer, _f64, _ptr, _where
 
 _COLL = {"bgk": L.RLB_BGK, "mrt": L.RLB_MRT}
 _PREC = {"fp64": L.RLB_FP64, "fp32": L.RLB_FP32_STORAGE}
@@ -53,6 +53,7 @@ class TubeBatch:
 
     def set_fields(self, e, ux, uy, uz, n):
         ts = [_f64(t) for t in (e, ux, uy, uz, n)]
+        _after_producer(self.stream, ts)
         L.rlb_batch_set_fields(self._b, *[_ptr(t) for t in ts], _where(ts[0]))
 
     def autotune(self, trial_steps=32):
@@ -79,4 +80,5 @@ class TubeBatch:
     def load_state(self, t):
         dt = torch.float64 if self.precision == "fp64" else torch.float32
         t = t.to(dt).contiguous()
+        _after_producer(self.stream, [t])
         L.rlb_batch_load_state(self._b, _ptr(t), _where(t))

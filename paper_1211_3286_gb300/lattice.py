@@ -25,6 +25,15 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
 
 
+def _after_producer(stream, ts):
+    """Device inputs may still be in flight on torch's current stream: order the
+    library's stream after it before librlb reads them."""
+    if stream is not None and any(t is not None and t.is_cuda for t in ts):
+        cur = torch.cuda.current_stream()
+        if cur.cuda_stream != stream.cuda_stream:
+            stream.wait_stream(cur)
+
+
 def _f64(t):
     if t is None:
         return None
@@ -81,6 +90,7 @@ class Lattice:
         dev = {t.is_cuda for t in ts}
         if len(dev) != 1:
             raise ValueError("all fields must live on the same side (host or device)")
+        _after_producer(self.stream, ts)
         L.rlb_set_fields(self._h, *[_ptr(t) for t in ts], _where(ts[0]))
 
     def step(self, nsteps=1):
@@ -111,6 +121,7 @@ class Lattice:
         t = t.to(dt).contiguous()
         if t.numel() * t.element_size() != L.rlb_state_bytes(self._h):
             raise ValueError("state has the wrong size")
+        _after_producer(self.stream, [t])
         L.rlb_load_state(self._h, _ptr(t), _where(t))
 
     def steps_done(self):
