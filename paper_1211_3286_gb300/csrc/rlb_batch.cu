@@ -10,7 +10,9 @@
 // exchange data, so no grid-wide barrier exists and no CTA waits on another.
 // A tube's two lattices (<= 2 x 486 KB at 3200 FP32 nodes) are re-read every step
 // through L2 (ld.global.cg / st.global.cg: coherent at L2 for the CTA's own
-// writes after __syncthreads).
+// writes after __syncthreads).  Whether they stay in L2 depends on how many tubes
+// are in flight: at two 256-thread CTAs per SM on the 1024-tube sweep the 304
+// tubes in flight exceed L2 and most bytes come from DRAM.
 //
 // Launch shape (threads per CTA, CTAs per SM) is picked by rlb_batch_autotune,
 // which times each candidate on a copy of the state.  rlb_batch_run replays
