@@ -78,7 +78,7 @@ __global__ void k_tubes(const TubeInfo* __restrict__ order, int ntubes, const St
           g[a] = ld_cg(src + (19ull + a) * nodes + i);
         }
         bool b;
-        if constexpr (sizeof(S) == 8) b = node_collide_f64<MRT, false>(f, g, k);
+        if constexpr (sizeof(S) == 8) b = node_collide_fx<MRT, false>(f, g, k);
         else b = node_collide_f32s<MRT, false>(f, g, k);
         if (b) atomicMin(bad, x0);
 #pragma unroll

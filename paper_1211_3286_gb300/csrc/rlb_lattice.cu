@@ -98,7 +98,8 @@ __global__ void __launch_bounds__(kBlockX, sizeof(S) == 8 ? 3 : 1) k_step(const 
   pull19<S>(src, geo.plane, xs, row, f);
   pull19<S>(src + 19ull * geo.plane, geo.plane, xs, row, g);
   bool b;
-  if constexpr (sizeof(S) == 8) b = node_collide_f64<MRT, QSEP, ETA>(f, g, k);
+  if constexpr (sizeof(S) == 8 && ETA) b = node_collide_f64<MRT, QSEP, true>(f, g, k);
+  else if constexpr (sizeof(S) == 8) b = node_collide_fx<MRT, QSEP>(f, g, k);
   else b = node_collide_f32s<MRT, QSEP>(f, g, k);
   const unsigned node = row[1][1] + (unsigned)x;
   if (b) atomicMin(bad, (unsigned long long)node);

@@ -32,6 +32,7 @@
 //       sum_axis g^eq = P,  sum_diag g^eq = P + 0.5 sigma u^2,
 //       q^eq_i = -(2/3) sigma u_i.
 #pragma once
+#include <cmath>
 #include <cstdint>
 
 namespace rlb {
@@ -72,6 +73,11 @@ struct StepConst {
   double eta_s;
   int tauf_local;
   double a_e, a_p, a_q;
+  // 64-bit fixed-point copies for the integer-pipe FP64 collide: omega * 2^63 (even),
+  // ce * 2^73, cp * 2^69, cq * 2^67 (|ce| < 2/2394, |cp| < 2/252, |cq| < 2/40 keep them
+  // below 2^63)
+  unsigned long long Om_f, Om_v;
+  long long CE, CP, CQ;
 };
 
 // q = 19 (D3Q19: weights 1/3, 1/18, 1/36; MRT row norms e 2394, eps 252, q 40) or
@@ -111,6 +117,11 @@ inline StepConst make_step_const(double tau_f, double tau_v, double tau_e, doubl
   k.gA_k_f = (float)k.gA_k; k.gD_k_f = (float)k.gD_k;
   k.gA_s_f = (float)k.gA_s; k.gD_s_f = (float)k.gD_s; k.gA_a_f = (float)k.gA_a; k.gD_a_f = (float)k.gD_a;
   k.ce_f = (float)k.ce; k.cp_f = (float)k.cp; k.cq_f = (float)k.cq;
+  k.Om_f = (unsigned long long)std::ldexp(k.omf, 63) & ~1ull;
+  k.Om_v = (unsigned long long)std::ldexp(k.omv, 63) & ~1ull;
+  k.CE = std::llround(std::ldexp(k.ce, 73));
+  k.CP = std::llround(std::ldexp(k.cp, 69));
+  k.CQ = std::llround(std::ldexp(k.cq, 67));
   return k;
 }
 
@@ -441,6 +452,275 @@ __device__ __forceinline__ bool node_collide_f64(double (&f)[19], double (&g)[19
     }
   }
   return m.bad;
+}
+
+// ----------------------------------------------------------------------------
+// FP64 collide in 64-bit block fixed point (integer pipe).
+//
+// GB300 retires 2 FP64 instructions per clock per SM but 64 integer ones, so the
+// per-link arithmetic of the FP64 step runs on integers.  The 19 values of one
+// distribution at one node are put on the grid of their largest binary exponent
+// E: x = X * 2^(E - 1079), |X| < 2^57 for the largest value.  Every value then
+// keeps its bits down to 2^-56 of the node's largest population.  Sums (Eq. 10),
+// equilibria (Eqs. 7-9), the BGK relaxation (Eqs. 5-6) and the MRT projection
+// (Eq. 35) are integer adds and 64 x 64 -> high-64 products, each off by at most a
+// few grid units; only the recovery (Eq. 10 inverted) runs in FP64.  Each output
+// is rounded once to FP64.
+//
+// Output rounding to FP64 has two routes: integer bit assembly (ALU pipe) or
+// __ll2double_rn (FP64 pipe).  RLB_FX_OUT_F / RLB_FX_OUT_G pick the route for the
+// f and g outputs (0 = integer, 1 = FP64 pipe) to balance the two pipes.
+#ifndef RLB_FX_OUT_F
+#define RLB_FX_OUT_F 1
+#endif
+#ifndef RLB_FX_OUT_G
+#define RLB_FX_OUT_G 1
+#endif
+
+namespace fx {
+
+constexpr unsigned long long kThird = 0x5555555555555556ull;       // ceil(2^64 / 3)
+constexpr unsigned long long kSixth = 0x2AAAAAAAAAAAAAABull;       // ceil(2^64 / 6)
+constexpr unsigned long long kTwoThirds = 0xAAAAAAAAAAAAAAABull;   // ceil(2^65 / 3)
+constexpr unsigned long long kEighteenth = 0x0E38E38E38E38E39ull;  // ceil(2^64 / 18)
+constexpr unsigned long long kSignBit = 0x8000000000000000ull;
+
+// floor(a b / 2^64) for unsigned a, b without the low partial products: low by at most 2.
+__device__ __forceinline__ unsigned long long mulhi(unsigned long long a, unsigned long long b) {
+  const unsigned a0 = (unsigned)a, a1 = (unsigned)(a >> 32), b0 = (unsigned)b, b1 = (unsigned)(b >> 32);
+  return (unsigned long long)a1 * b1 + ((unsigned long long)__umulhi(a1, b0) + __umulhi(a0, b1));
+}
+// y b / 2^64 for signed y (|y| < 2^63) and unsigned b: y + 2^63 is y with its top bit
+// flipped, and the bias adds b / 2 to the product (bh = b >> 1).
+__device__ __forceinline__ long long mulhi_su(long long y, unsigned long long b, unsigned long long bh) {
+  return (long long)(mulhi((unsigned long long)y ^ kSignBit, b) - bh);
+}
+// v with the sign s (0 or 1)
+__device__ __forceinline__ long long with_sign(unsigned long long v, unsigned s) {
+  const unsigned long long m = 0ull - (unsigned long long)s;
+  return (long long)((v ^ m) - m);
+}
+
+// |x| * 2^(Er - 1086), truncated, for a double x whose biased exponent is at most Er:
+// the 53-bit significand top-aligned in 64 bits and shifted right by Er - exponent.
+// Zero and subnormal inputs give 0 when Er >= 64.
+__device__ __forceinline__ unsigned long long to_fixed_abs(double x, int Er) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned r = (unsigned)(Er - (int)((hi >> 20) & 0x7ffu));
+  const unsigned th = __funnelshift_l(lo, hi, 11) | 0x80000000u;
+  const unsigned tl = lo << 11;
+  const unsigned vh = __funnelshift_rc(th, 0u, r);
+  const unsigned vl = r < 32u ? __funnelshift_rc(tl, th, r) : __funnelshift_rc(th, 0u, r - 32u);
+  return ((unsigned long long)vh << 32) | vl;
+}
+__device__ __forceinline__ long long to_fixed(double x, int Er) {
+  return with_sign(to_fixed_abs(x, Er), (unsigned)__double2hiint(x) >> 31);
+}
+
+// K * 2^(E - 1079) rounded to the nearest double (ties away from zero) by integer
+// bit assembly; K = 0 gives +0.  Needs E >= 57 so that the result is normal.
+__device__ __forceinline__ double from_fixed_int(long long K, int E) {
+  const unsigned long long s = (unsigned long long)(K >> 63);
+  const unsigned long long a = ((unsigned long long)K ^ s) - s;
+  const int lz = __clzll((long long)a);
+  const unsigned long long n = a << (lz & 63);
+  const unsigned long long m = (n >> 11) + ((n >> 10) & 1ull);
+  const unsigned long long bits = m + ((unsigned long long)(unsigned)(E + 6 - lz) << 52) + (s << 63);
+  return a ? __longlong_as_double((long long)bits) : 0.0;
+}
+// The same through the FP64 pipe's int64 conversion (round to nearest even).
+__device__ __forceinline__ double from_fixed_dp(long long K, int E) {
+  const double d = __ll2double_rn(K);
+  const int hi = __double2hiint(d);
+  return __hiloint2double(K ? hi + (int)((unsigned)(E - 1079) << 20) : hi, __double2loint(d));
+}
+template <int DP>
+__device__ __forceinline__ double from_fixed(long long K, int E) {
+  if constexpr (DP) return from_fixed_dp(K, E);
+  else return from_fixed_int(K, E);
+}
+
+// One relaxation X - omega (X - X^eq) + c with Om = omega 2^63: the biased product
+// mulhi(2 (X - X^eq) + 2^63, Om) is omega (X - X^eq) + Om / 2, and c carries + Om / 2.
+__device__ __forceinline__ long long relax(long long X, long long Xeq, unsigned long long Om, long long c) {
+  const unsigned long long y = (unsigned long long)(X - Xeq) << 1;
+  return X - (long long)mulhi(y ^ kSignBit, Om) + c;
+}
+
+// Per-distribution equilibrium pieces on its grid (Eqs. 7-9 split per link pair):
+//   axis pair i:   ev = KA + X_i,                          od = Z_i
+//   diagonal i,j:  ev = KA/2 + (X_i + X_j)/2 +- Y_ij,       od = (Z_i +- Z_j)/2
+// with X_i = D u_i^2 / 4, Y_ij = D u_i u_j / 4, Z_i = D u_i / 6 for the density D
+// (sigma for g, N0 for f).
+struct EqPieces {
+  long long KA, Xx, Xy, Xz, Yxy, Yxz, Yyz, Zx, Zy, Zz;
+};
+struct UFix {
+  unsigned long long ax, ay, az;       // |u_i| 2^63
+  unsigned sx, sy, sz;                 // sign bits
+  unsigned long long xx, yy, zz;       // u_i^2 2^62
+  unsigned long long xy, xz, yz;       // |u_i u_j| 2^62
+};
+__device__ __forceinline__ void eq_pieces(unsigned long long D, const UFix& u, EqPieces& q) {
+  q.Xx = (long long)mulhi(D, u.xx);
+  q.Xy = (long long)mulhi(D, u.yy);
+  q.Xz = (long long)mulhi(D, u.zz);
+  q.Yxy = with_sign(mulhi(D, u.xy), u.sx ^ u.sy);
+  q.Yxz = with_sign(mulhi(D, u.xz), u.sx ^ u.sz);
+  q.Yyz = with_sign(mulhi(D, u.yz), u.sy ^ u.sz);
+  const unsigned long long D3 = mulhi(D, kThird);
+  q.Zx = with_sign(mulhi(D3, u.ax), u.sx);
+  q.Zy = with_sign(mulhi(D3, u.ay), u.sy);
+  q.Zz = with_sign(mulhi(D3, u.az), u.sz);
+}
+
+// Relax the 18 moving links of one distribution: class constants cA (axis) and cD
+// (diagonal) hold Om / 2 plus any MRT class correction, dq the odd corrections.
+template <int DP, bool ODD>
+__device__ __forceinline__ void relax_links(const long long (&X)[19], const EqPieces& q, unsigned long long Om,
+                                            long long cA, long long cD, const long long (&dq)[9], int E,
+                                            double (&out)[19]) {
+  const long long ev[9] = {q.KA + q.Xx, q.KA + q.Xy, q.KA + q.Xz,
+                           (q.KA >> 1) + ((q.Xx + q.Xy) >> 1) + q.Yxy, (q.KA >> 1) + ((q.Xx + q.Xy) >> 1) - q.Yxy,
+                           (q.KA >> 1) + ((q.Xx + q.Xz) >> 1) + q.Yxz, (q.KA >> 1) + ((q.Xx + q.Xz) >> 1) - q.Yxz,
+                           (q.KA >> 1) + ((q.Xy + q.Xz) >> 1) + q.Yyz, (q.KA >> 1) + ((q.Xy + q.Xz) >> 1) - q.Yyz};
+  const long long od[9] = {q.Zx, q.Zy, q.Zz,
+                           (q.Zx + q.Zy) >> 1, (q.Zx - q.Zy) >> 1, (q.Zx + q.Zz) >> 1, (q.Zx - q.Zz) >> 1,
+                           (q.Zy + q.Zz) >> 1, (q.Zy - q.Zz) >> 1};
+#pragma unroll
+  for (int p = 0; p < 9; ++p) {
+    const long long c = p < 3 ? cA : cD;
+    const long long d = ODD ? dq[p] : 0;
+    out[2 * p + 1] = from_fixed<DP>(relax(X[2 * p + 1], ev[p] + od[p], Om, c + d), E);
+    out[2 * p + 2] = from_fixed<DP>(relax(X[2 * p + 2], ev[p] - od[p], Om, c - d), E);
+  }
+}
+
+}  // namespace fx
+
+// FP64 node collide on the integer pipe: moments, recovery (FP64), equilibria, BGK f,
+// BGK / MRT g.  Same contract and results (to a few units of 2^-56 of the node's
+// largest population per link) as node_collide_f64 with constant relaxation times.
+template <bool MRT, bool QSEP>
+__device__ __forceinline__ bool node_collide_fx(double (&f)[19], double (&g)[19], const StepConst& k) {
+  using namespace fx;
+  unsigned mg = 0, mf = 0;
+#pragma unroll
+  for (int a = 0; a < 19; ++a) {
+    mg = max(mg, (unsigned)__double2hiint(g[a]) & 0x7ff00000u);
+    mf = max(mf, (unsigned)__double2hiint(f[a]) & 0x7ff00000u);
+  }
+  const int Eg = (int)(mg >> 20), Ef = (int)(mf >> 20);
+  long long G[19], F[19];
+#pragma unroll
+  for (int a = 0; a < 19; ++a) {
+    G[a] = to_fixed(g[a], Eg + 7);
+    F[a] = to_fixed(f[a], Ef + 7);
+  }
+  // conserved sums (Eq. 10), exact on the grid
+  long long sp[9], dp[9];
+#pragma unroll
+  for (int p = 0; p < 9; ++p) {
+    sp[p] = G[2 * p + 1] + G[2 * p + 2];
+    dp[p] = G[2 * p + 1] - G[2 * p + 2];
+  }
+  const long long Sa = sp[0] + sp[1] + sp[2];
+  const long long Sd = ((sp[3] + sp[4]) + (sp[5] + sp[6])) + (sp[7] + sp[8]);
+  const long long T00 = G[0] + Sa + Sd;
+  const long long Mx = dp[0] + dp[3] + dp[4] + dp[5] + dp[6];
+  const long long My = dp[1] + dp[3] - dp[4] + dp[7] + dp[8];
+  const long long Mz = dp[2] + dp[5] - dp[6] + dp[7] - dp[8];
+  long long N0 = F[0];
+#pragma unroll
+  for (int a = 1; a < 19; ++a) N0 += F[a];
+
+  // recovery (Eq. 10 inverted under P = e/3) in FP64 on the once-rounded sums:
+  // A/4 = T00^2 - (3/4)|M|^2, H = T00 + sqrt(A/4) = 3 sigma / 2, w = M / H = 2 u / 3
+  const double t00 = from_fixed_dp(T00, Eg);
+  const double mx = from_fixed_dp(Mx, Eg), my = from_fixed_dp(My, Eg), mz = from_fixed_dp(Mz, Eg);
+  const double MM = fma(mx, mx, fma(my, my, mz * mz));
+  const double A4 = fma(t00, t00, -0.75 * MM);
+  const double H = t00 + sqrt_seeded(A4);
+  const double iH = rcp_seeded(H);
+  const double wx = mx * iH, wy = my * iH, wz = mz * iH;
+
+  // back to the grid: sigma = 2H/3, P = sigma - T00; |u_i| 2^63 = 3/2 |w_i| 2^63
+  const unsigned long long sig = mulhi(to_fixed_abs(H, Eg + 7), kTwoThirds);
+  const long long Pf = (long long)sig - T00;
+  UFix u;
+  {
+    const unsigned long long ax = to_fixed_abs(wx, 1023), ay = to_fixed_abs(wy, 1023), az = to_fixed_abs(wz, 1023);
+    u.ax = ax + (ax >> 1);
+    u.ay = ay + (ay >> 1);
+    u.az = az + (az >> 1);
+    u.sx = (unsigned)__double2hiint(wx) >> 31;
+    u.sy = (unsigned)__double2hiint(wy) >> 31;
+    u.sz = (unsigned)__double2hiint(wz) >> 31;
+    u.xx = mulhi(u.ax, u.ax);
+    u.yy = mulhi(u.ay, u.ay);
+    u.zz = mulhi(u.az, u.az);
+    u.xy = mulhi(u.ax, u.ay);
+    u.xz = mulhi(u.ax, u.az);
+    u.yz = mulhi(u.ay, u.az);
+  }
+  const unsigned long long u2 = u.xx + u.yy + u.zz;   // u^2 2^62
+  // non-physical: A < 0 (or not finite), T00 <= 0, P <= 0, u^2 >= 1, or a block
+  // exponent outside the normal range the grid needs
+  const bool bad = (Eg < 64) | (Eg > 2046) | (Ef < 64) | (Ef > 2046) |
+                   ((unsigned)__double2hiint(A4) >= 0x7ff00000u) | (T00 <= 0) | (Pf <= 0) | (u2 >= (1ull << 62));
+
+  const long long dq0[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  // ---- g (Eq. 6 or Eq. 35 with Eqs. 8-9)
+  {
+    EqPieces q;
+    eq_pieces(sig, u, q);
+    const long long SX = q.Xx + q.Xy + q.Xz;                                  // sigma u^2 / 4
+    q.KA = (long long)mulhi((unsigned long long)Pf, kSixth) - (long long)mulhi((unsigned long long)SX, kThird);
+    const long long geq0 = (long long)sig - 3 * Pf - 2 * SX;                   // sigma - 3P - sigma u^2 / 2
+    const unsigned long long Om = k.Om_v;
+    long long c0 = (long long)(Om >> 1), cA = c0, cD = c0;
+    long long dq[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    if (MRT) {
+      // e and eps projections of g - g^eq from the class sums (sum_axis g^eq = P,
+      // sum_diag g^eq = P + sigma u^2 / 2), taken at 1/8 scale against overflow
+      const long long n0 = (G[0] - geq0) >> 3;
+      const long long nA = (Sa - Pf) >> 3;
+      const long long nD = (Sd - Pf - 2 * SX) >> 3;
+      const long long ae = __mul64hi(8 * nD - 11 * nA - 30 * n0, k.CE) >> 6;   // ce (M_e . (g - g^eq))
+      const long long ap = __mul64hi(nD - 4 * nA + 12 * n0, k.CP) >> 2;        // cp (M_eps . (g - g^eq))
+      c0 += 30 * ae - 12 * ap;
+      cA += 11 * ae + 4 * ap;
+      cD -= 8 * ae + ap;
+      if (QSEP) {
+        // energy-flux rows q_i = (5|c|^2 - 9) c_i, q^eq_i = -(2/3) M_i
+        const unsigned long long h23 = kTwoThirds >> 1;
+        const long long vx = ((Mx - 5 * dp[0]) >> 2) + (mulhi_su(Mx, kTwoThirds, h23) >> 2);
+        const long long vy = ((My - 5 * dp[1]) >> 2) + (mulhi_su(My, kTwoThirds, h23) >> 2);
+        const long long vz = ((Mz - 5 * dp[2]) >> 2) + (mulhi_su(Mz, kTwoThirds, h23) >> 2);
+        const long long aqx = __mul64hi(vx, k.CQ) >> 1, aqy = __mul64hi(vy, k.CQ) >> 1, aqz = __mul64hi(vz, k.CQ) >> 1;
+        dq[0] = 4 * aqx; dq[1] = 4 * aqy; dq[2] = 4 * aqz;
+        dq[3] = -(aqx + aqy); dq[4] = -(aqx - aqy);
+        dq[5] = -(aqx + aqz); dq[6] = -(aqx - aqz);
+        dq[7] = -(aqy + aqz); dq[8] = -(aqy - aqz);
+      }
+    }
+    g[0] = from_fixed<RLB_FX_OUT_G>(relax(G[0], geq0, Om, c0), Eg);
+    relax_links<RLB_FX_OUT_G, MRT && QSEP>(G, q, Om, cA, cD, dq, Eg, g);
+  }
+  // ---- f (Eq. 5 with Eq. 7)
+  {
+    EqPieces q;
+    const unsigned long long n0u = (unsigned long long)N0;
+    eq_pieces(n0u, u, q);
+    const long long SX = q.Xx + q.Xy + q.Xz;                                  // N0 u^2 / 4
+    q.KA = (long long)mulhi(n0u, kEighteenth) - (long long)mulhi((unsigned long long)SX, kThird);
+    const long long feq0 = (long long)mulhi(n0u, kThird) - 2 * SX;            // N0/3 - N0 u^2 / 2
+    const unsigned long long Om = k.Om_f;
+    const long long c = (long long)(Om >> 1);
+    f[0] = from_fixed<RLB_FX_OUT_F>(relax(F[0], feq0, Om, c), Ef);
+    relax_links<RLB_FX_OUT_F, false>(F, q, Om, c, c, dq0, Ef, f);
+  }
+  return bad;
 }
 
 // ----------------------------------------------------------------------------
