@@ -78,8 +78,14 @@ __device__ __forceinline__ void pull19(const S* __restrict__ base, unsigned long
   }
 }
 
+// Resident 128-thread blocks per SM the FP64 step is compiled for (register cap
+// 65536 / (128 x blocks)).
+#ifndef RLB_F64_BLOCKS_PER_SM
+#define RLB_F64_BLOCKS_PER_SM 3
+#endif
+
 template <typename S, bool MRT, bool QSEP, bool ETA = false>
-__global__ void __launch_bounds__(kBlockX, sizeof(S) == 8 ? 3 : 1) k_step(const S* __restrict__ src, S* __restrict__ dst, Geo geo,
+__global__ void __launch_bounds__(kBlockX, sizeof(S) == 8 ? RLB_F64_BLOCKS_PER_SM : 1) k_step(const S* __restrict__ src, S* __restrict__ dst, Geo geo,
                                                   StepConst k, unsigned long long* __restrict__ bad) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= geo.nx) return;
@@ -108,6 +114,156 @@ __global__ void __launch_bounds__(kBlockX, sizeof(S) == 8 ? 3 : 1) k_step(const 
     dst[(unsigned long long)a * geo.plane + node] = f[a];
     dst[(19ull + a) * geo.plane + node] = g[a];
   }
+}
+
+// FP64 step with warp roles (the integer-pipe collide of rlb_node.cuh).  A block of
+// 2 W warps serves 32 W nodes along x: warps [0, W) pull and relax g, warps [W, 2W)
+// pull and relax f of the same nodes.  The g warps recover u (Eq. 10 inverted) and
+// hand it to the f warps through shared memory across one block barrier.  Each
+// thread holds one distribution of one node, so twice as many warps fit in the
+// registers the single-role kernel needs; out-of-range threads (x >= nx) pull a
+// clamped node, pass the barrier and store nothing.
+#ifndef RLB_WS_BLOCKS_PER_SM
+#define RLB_WS_BLOCKS_PER_SM 5
+#endif
+
+template <int W, bool MRT, bool QSEP>
+__global__ void __launch_bounds__(64 * W, RLB_WS_BLOCKS_PER_SM * 2 / W)
+    k_step_ws(const double* __restrict__ src, double* __restrict__ dst, Geo geo, StepConst k,
+              unsigned long long* __restrict__ bad) {
+  __shared__ unsigned long long s_ax[32 * W], s_ay[32 * W], s_az[32 * W];
+  __shared__ unsigned s_sg[32 * W];
+  const int warp = threadIdx.x >> 5;
+  const bool is_g = warp < W;
+  const int slot = (is_g ? warp : warp - W) * 32 + (threadIdx.x & 31);
+  const int x0 = blockIdx.x * (32 * W) + slot;
+  const bool valid = x0 < geo.nx;
+  const int x = valid ? x0 : geo.nx - 1;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const int xs[3] = {src_minus(x, geo.nx, geo.bcx), x, src_plus(x, geo.nx, geo.bcx)};
+  const int ys[3] = {src_minus(y, geo.ny, geo.bcy), y, src_plus(y, geo.ny, geo.bcy)};
+  const int zs[3] = {src_minus(z, geo.nz, geo.bcz), z, src_plus(z, geo.nz, geo.bcz)};
+  unsigned row[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) row[i][j] = ((unsigned)zs[i] * (unsigned)geo.ny + (unsigned)ys[j]) * (unsigned)geo.nx;
+  const unsigned long long plane0 = is_g ? 19ull * geo.plane : 0ull;
+  double v[19];
+  pull19<double>(src + plane0, geo.plane, xs, row, v);
+
+  using namespace fx;
+  // both roles: block exponent and fixed-point values
+  unsigned me = 0;
+#pragma unroll
+  for (int a = 0; a < 19; ++a) me = max(me, (unsigned)__double2hiint(v[a]) & 0x7ff00000u);
+  const int E = (int)(me >> 20);
+  long long X[19];
+#pragma unroll
+  for (int a = 0; a < 19; ++a) X[a] = to_fixed(v[a], E + 7);
+
+  UFix u;
+  long long Sa = 0, Sd = 0, T00 = 0, Mx = 0, My = 0, Mz = 0, Pf = 0, dp0 = 0, dp1 = 0, dp2 = 0, N0 = 0;
+  unsigned long long sig = 0;
+  bool b = (E < 64) | (E > 2046);
+  if (is_g) {
+    // conserved sums (Eq. 10) and the recovery in FP64 on the once-rounded sums
+    long long sp[9], dp[9];
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+      sp[p] = X[2 * p + 1] + X[2 * p + 2];
+      dp[p] = X[2 * p + 1] - X[2 * p + 2];
+    }
+    dp0 = dp[0]; dp1 = dp[1]; dp2 = dp[2];
+    Sa = sp[0] + sp[1] + sp[2];
+    Sd = ((sp[3] + sp[4]) + (sp[5] + sp[6])) + (sp[7] + sp[8]);
+    T00 = X[0] + Sa + Sd;
+    Mx = dp[0] + dp[3] + dp[4] + dp[5] + dp[6];
+    My = dp[1] + dp[3] - dp[4] + dp[7] + dp[8];
+    Mz = dp[2] + dp[5] - dp[6] + dp[7] - dp[8];
+    const double t00 = from_fixed_dp(T00, E);
+    const double mx = from_fixed_dp(Mx, E), my = from_fixed_dp(My, E), mz = from_fixed_dp(Mz, E);
+    const double MM = fma(mx, mx, fma(my, my, mz * mz));
+    const double A4 = fma(t00, t00, -0.75 * MM);
+    const double H = t00 + sqrt_seeded(A4);
+    const double iH = rcp_seeded(H);
+    const double wx = mx * iH, wy = my * iH, wz = mz * iH;
+    sig = mulhi(to_fixed_abs(H, E + 7), kTwoThirds);
+    Pf = (long long)sig - T00;
+    const unsigned long long ax = to_fixed_abs(wx, 1023), ay = to_fixed_abs(wy, 1023), az = to_fixed_abs(wz, 1023);
+    u.ax = ax + (ax >> 1);
+    u.ay = ay + (ay >> 1);
+    u.az = az + (az >> 1);
+    u.sx = (unsigned)__double2hiint(wx) >> 31;
+    u.sy = (unsigned)__double2hiint(wy) >> 31;
+    u.sz = (unsigned)__double2hiint(wz) >> 31;
+    s_ax[slot] = u.ax;
+    s_ay[slot] = u.ay;
+    s_az[slot] = u.az;
+    s_sg[slot] = u.sx | (u.sy << 1) | (u.sz << 2);
+    ufix_products(u);
+    b |= ((unsigned)__double2hiint(A4) >= 0x7ff00000u) | (T00 <= 0) | (Pf <= 0) | (u.xx + u.yy + u.zz >= (1ull << 62));
+  } else {
+    N0 = X[0];
+#pragma unroll
+    for (int a = 1; a < 19; ++a) N0 += X[a];
+  }
+  __syncthreads();
+  if (!is_g) {
+    u.ax = s_ax[slot];
+    u.ay = s_ay[slot];
+    u.az = s_az[slot];
+    const unsigned sg = s_sg[slot];
+    u.sx = sg & 1u;
+    u.sy = (sg >> 1) & 1u;
+    u.sz = sg >> 2;
+    ufix_products(u);
+  }
+
+  // equilibria (Eqs. 7-9) and the relaxation constants of this role
+  EqPieces q;
+  eq_pieces(is_g ? sig : (unsigned long long)N0, u, q);
+  const long long SX = q.Xx + q.Xy + q.Xz;             // D u^2 / 4
+  long long eq0;
+  if (is_g) {
+    q.KA = (long long)mulhi((unsigned long long)Pf, kSixth) - (long long)mulhi((unsigned long long)SX, kThird);
+    eq0 = (long long)sig - 3 * Pf - 2 * SX;             // sigma - 3P - sigma u^2 / 2
+  } else {
+    q.KA = (long long)mulhi((unsigned long long)N0, kEighteenth) - (long long)mulhi((unsigned long long)SX, kThird);
+    eq0 = (long long)mulhi((unsigned long long)N0, kThird) - 2 * SX;   // N0/3 - N0 u^2 / 2
+  }
+  const unsigned long long Om = is_g ? k.Om_v : k.Om_f;
+  long long c0 = (long long)(Om >> 1), cA = c0, cD = c0;
+  long long dq[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  if (MRT && is_g) {
+    // e and eps projections of g - g^eq from the class sums, at 1/8 scale
+    const long long n0 = (X[0] - eq0) >> 3;
+    const long long nA = (Sa - Pf) >> 3;
+    const long long nD = (Sd - Pf - 2 * SX) >> 3;
+    const long long ae = __mul64hi(8 * nD - 11 * nA - 30 * n0, k.CE) >> 6;
+    const long long ap = __mul64hi(nD - 4 * nA + 12 * n0, k.CP) >> 2;
+    c0 += 30 * ae - 12 * ap;
+    cA += 11 * ae + 4 * ap;
+    cD -= 8 * ae + ap;
+    if (QSEP) {
+      const unsigned long long h23 = kTwoThirds >> 1;
+      const long long vx = ((Mx - 5 * dp0) >> 2) + (mulhi_su(Mx, kTwoThirds, h23) >> 2);
+      const long long vy = ((My - 5 * dp1) >> 2) + (mulhi_su(My, kTwoThirds, h23) >> 2);
+      const long long vz = ((Mz - 5 * dp2) >> 2) + (mulhi_su(Mz, kTwoThirds, h23) >> 2);
+      const long long aqx = __mul64hi(vx, k.CQ) >> 1, aqy = __mul64hi(vy, k.CQ) >> 1, aqz = __mul64hi(vz, k.CQ) >> 1;
+      dq[0] = 4 * aqx; dq[1] = 4 * aqy; dq[2] = 4 * aqz;
+      dq[3] = -(aqx + aqy); dq[4] = -(aqx - aqy);
+      dq[5] = -(aqx + aqz); dq[6] = -(aqx - aqz);
+      dq[7] = -(aqy + aqz); dq[8] = -(aqy - aqz);
+    }
+  }
+  v[0] = from_fixed<RLB_FX_OUT_G>(relax(X[0], eq0, Om, c0), E);
+  relax_links<RLB_FX_OUT_G, MRT && QSEP>(X, q, Om, cA, cD, dq, E, v);
+  if (!valid) return;
+  const unsigned node = row[1][1] + (unsigned)x;
+  if (b) atomicMin(bad, (unsigned long long)node);
+#pragma unroll
+  for (int a = 0; a < 19; ++a) dst[plane0 + (unsigned long long)a * geo.plane + node] = v[a];
 }
 
 // D2Q9 pull of the 9 f and 9 g arriving at node (x, y).
@@ -283,10 +439,28 @@ cudaError_t launch_step(rlb_handle* h, const void* src, void* dst, cudaStream_t 
       return cudaGetLastError();
     }
   }
-  if (!mrt) k_step<S, false, false><<<grid, bx, 0, st>>>(s, d, geo, h->k, h->d_bad);
-  else if (!q) k_step<S, true, false><<<grid, bx, 0, st>>>(s, d, geo, h->k, h->d_bad);
-  else k_step<S, true, true><<<grid, bx, 0, st>>>(s, d, geo, h->k, h->d_bad);
-  return cudaGetLastError();
+  if constexpr (sizeof(S) == 8) {
+    // warp roles: 64-thread blocks (one g and one f warp) for small lattices
+    const double* s8 = (const double*)src;
+    double* d8 = (double*)dst;
+    if (bx == 32) {
+      dim3 gw((geo.nx + 31) / 32, geo.ny, geo.nz);
+      if (!mrt) k_step_ws<1, false, false><<<gw, 64, 0, st>>>(s8, d8, geo, h->k, h->d_bad);
+      else if (!q) k_step_ws<1, true, false><<<gw, 64, 0, st>>>(s8, d8, geo, h->k, h->d_bad);
+      else k_step_ws<1, true, true><<<gw, 64, 0, st>>>(s8, d8, geo, h->k, h->d_bad);
+    } else {
+      dim3 gw((geo.nx + 63) / 64, geo.ny, geo.nz);
+      if (!mrt) k_step_ws<2, false, false><<<gw, 128, 0, st>>>(s8, d8, geo, h->k, h->d_bad);
+      else if (!q) k_step_ws<2, true, false><<<gw, 128, 0, st>>>(s8, d8, geo, h->k, h->d_bad);
+      else k_step_ws<2, true, true><<<gw, 128, 0, st>>>(s8, d8, geo, h->k, h->d_bad);
+    }
+    return cudaGetLastError();
+  } else {
+    if (!mrt) k_step<S, false, false><<<grid, bx, 0, st>>>(s, d, geo, h->k, h->d_bad);
+    else if (!q) k_step<S, true, false><<<grid, bx, 0, st>>>(s, d, geo, h->k, h->d_bad);
+    else k_step<S, true, true><<<grid, bx, 0, st>>>(s, d, geo, h->k, h->d_bad);
+    return cudaGetLastError();
+  }
 }
 
 int check_flag(rlb_handle* h) {

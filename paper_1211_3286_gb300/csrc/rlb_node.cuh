@@ -598,129 +598,168 @@ __device__ __forceinline__ void relax_links(const long long (&X)[19], const EqPi
 
 }  // namespace fx
 
-// FP64 node collide on the integer pipe: moments, recovery (FP64), equilibria, BGK f,
-// BGK / MRT g.  Same contract and results (to a few units of 2^-56 of the node's
-// largest population per link) as node_collide_f64 with constant relaxation times.
-template <bool MRT, bool QSEP>
-__device__ __forceinline__ bool node_collide_fx(double (&f)[19], double (&g)[19], const StepConst& k) {
+using fx::EqPieces;
+using fx::UFix;
+
+// Velocity on the fixed grid: |u_i| 2^63 and sign bits, and the six products
+// u_i^2 2^62, |u_i u_j| 2^62 the equilibria need.
+__device__ __forceinline__ void ufix_products(UFix& u) {
+  using fx::mulhi;
+  u.xx = mulhi(u.ax, u.ax);
+  u.yy = mulhi(u.ay, u.ay);
+  u.zz = mulhi(u.az, u.az);
+  u.xy = mulhi(u.ax, u.ay);
+  u.xz = mulhi(u.ax, u.az);
+  u.yz = mulhi(u.ay, u.az);
+}
+
+// g half of the integer-pipe FP64 collide: block exponent, fixed-point values, the
+// conserved sums (Eq. 10, exact on the grid), the recovery (Eq. 10 inverted under
+// P = e/3) in FP64 on the once-rounded sums, and u on the fixed grid.
+struct GState {
+  long long G[19];
+  long long dp[3];            // pair differences of the axis pairs (energy-flux rows)
+  long long Sa, Sd, T00, Mx, My, Mz, Pf;
+  unsigned long long sig;     // sigma on the grid
+  int Eg;
+  bool bad;
+};
+__device__ __forceinline__ void fx_g_recover(const double (&g)[19], GState& s, UFix& u) {
   using namespace fx;
-  unsigned mg = 0, mf = 0;
+  unsigned mg = 0;
 #pragma unroll
-  for (int a = 0; a < 19; ++a) {
-    mg = max(mg, (unsigned)__double2hiint(g[a]) & 0x7ff00000u);
-    mf = max(mf, (unsigned)__double2hiint(f[a]) & 0x7ff00000u);
-  }
-  const int Eg = (int)(mg >> 20), Ef = (int)(mf >> 20);
-  long long G[19], F[19];
+  for (int a = 0; a < 19; ++a) mg = max(mg, (unsigned)__double2hiint(g[a]) & 0x7ff00000u);
+  s.Eg = (int)(mg >> 20);
 #pragma unroll
-  for (int a = 0; a < 19; ++a) {
-    G[a] = to_fixed(g[a], Eg + 7);
-    F[a] = to_fixed(f[a], Ef + 7);
-  }
-  // conserved sums (Eq. 10), exact on the grid
+  for (int a = 0; a < 19; ++a) s.G[a] = to_fixed(g[a], s.Eg + 7);
   long long sp[9], dp[9];
 #pragma unroll
   for (int p = 0; p < 9; ++p) {
-    sp[p] = G[2 * p + 1] + G[2 * p + 2];
-    dp[p] = G[2 * p + 1] - G[2 * p + 2];
+    sp[p] = s.G[2 * p + 1] + s.G[2 * p + 2];
+    dp[p] = s.G[2 * p + 1] - s.G[2 * p + 2];
   }
-  const long long Sa = sp[0] + sp[1] + sp[2];
-  const long long Sd = ((sp[3] + sp[4]) + (sp[5] + sp[6])) + (sp[7] + sp[8]);
-  const long long T00 = G[0] + Sa + Sd;
-  const long long Mx = dp[0] + dp[3] + dp[4] + dp[5] + dp[6];
-  const long long My = dp[1] + dp[3] - dp[4] + dp[7] + dp[8];
-  const long long Mz = dp[2] + dp[5] - dp[6] + dp[7] - dp[8];
-  long long N0 = F[0];
-#pragma unroll
-  for (int a = 1; a < 19; ++a) N0 += F[a];
-
-  // recovery (Eq. 10 inverted under P = e/3) in FP64 on the once-rounded sums:
+  s.dp[0] = dp[0]; s.dp[1] = dp[1]; s.dp[2] = dp[2];
+  s.Sa = sp[0] + sp[1] + sp[2];
+  s.Sd = ((sp[3] + sp[4]) + (sp[5] + sp[6])) + (sp[7] + sp[8]);
+  s.T00 = s.G[0] + s.Sa + s.Sd;
+  s.Mx = dp[0] + dp[3] + dp[4] + dp[5] + dp[6];
+  s.My = dp[1] + dp[3] - dp[4] + dp[7] + dp[8];
+  s.Mz = dp[2] + dp[5] - dp[6] + dp[7] - dp[8];
   // A/4 = T00^2 - (3/4)|M|^2, H = T00 + sqrt(A/4) = 3 sigma / 2, w = M / H = 2 u / 3
-  const double t00 = from_fixed_dp(T00, Eg);
-  const double mx = from_fixed_dp(Mx, Eg), my = from_fixed_dp(My, Eg), mz = from_fixed_dp(Mz, Eg);
+  const double t00 = from_fixed_dp(s.T00, s.Eg);
+  const double mx = from_fixed_dp(s.Mx, s.Eg), my = from_fixed_dp(s.My, s.Eg), mz = from_fixed_dp(s.Mz, s.Eg);
   const double MM = fma(mx, mx, fma(my, my, mz * mz));
   const double A4 = fma(t00, t00, -0.75 * MM);
   const double H = t00 + sqrt_seeded(A4);
   const double iH = rcp_seeded(H);
   const double wx = mx * iH, wy = my * iH, wz = mz * iH;
-
-  // back to the grid: sigma = 2H/3, P = sigma - T00; |u_i| 2^63 = 3/2 |w_i| 2^63
-  const unsigned long long sig = mulhi(to_fixed_abs(H, Eg + 7), kTwoThirds);
-  const long long Pf = (long long)sig - T00;
-  UFix u;
-  {
-    const unsigned long long ax = to_fixed_abs(wx, 1023), ay = to_fixed_abs(wy, 1023), az = to_fixed_abs(wz, 1023);
-    u.ax = ax + (ax >> 1);
-    u.ay = ay + (ay >> 1);
-    u.az = az + (az >> 1);
-    u.sx = (unsigned)__double2hiint(wx) >> 31;
-    u.sy = (unsigned)__double2hiint(wy) >> 31;
-    u.sz = (unsigned)__double2hiint(wz) >> 31;
-    u.xx = mulhi(u.ax, u.ax);
-    u.yy = mulhi(u.ay, u.ay);
-    u.zz = mulhi(u.az, u.az);
-    u.xy = mulhi(u.ax, u.ay);
-    u.xz = mulhi(u.ax, u.az);
-    u.yz = mulhi(u.ay, u.az);
-  }
-  const unsigned long long u2 = u.xx + u.yy + u.zz;   // u^2 2^62
+  // sigma = 2H/3, P = sigma - T00; |u_i| 2^63 = 3/2 |w_i| 2^63
+  s.sig = mulhi(to_fixed_abs(H, s.Eg + 7), kTwoThirds);
+  s.Pf = (long long)s.sig - s.T00;
+  const unsigned long long ax = to_fixed_abs(wx, 1023), ay = to_fixed_abs(wy, 1023), az = to_fixed_abs(wz, 1023);
+  u.ax = ax + (ax >> 1);
+  u.ay = ay + (ay >> 1);
+  u.az = az + (az >> 1);
+  u.sx = (unsigned)__double2hiint(wx) >> 31;
+  u.sy = (unsigned)__double2hiint(wy) >> 31;
+  u.sz = (unsigned)__double2hiint(wz) >> 31;
+  ufix_products(u);
   // non-physical: A < 0 (or not finite), T00 <= 0, P <= 0, u^2 >= 1, or a block
   // exponent outside the normal range the grid needs
-  const bool bad = (Eg < 64) | (Eg > 2046) | (Ef < 64) | (Ef > 2046) |
-                   ((unsigned)__double2hiint(A4) >= 0x7ff00000u) | (T00 <= 0) | (Pf <= 0) | (u2 >= (1ull << 62));
+  s.bad = (s.Eg < 64) | (s.Eg > 2046) | ((unsigned)__double2hiint(A4) >= 0x7ff00000u) | (s.T00 <= 0) |
+          (s.Pf <= 0) | (u.xx + u.yy + u.zz >= (1ull << 62));
+}
 
-  const long long dq0[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-  // ---- g (Eq. 6 or Eq. 35 with Eqs. 8-9)
-  {
-    EqPieces q;
-    eq_pieces(sig, u, q);
-    const long long SX = q.Xx + q.Xy + q.Xz;                                  // sigma u^2 / 4
-    q.KA = (long long)mulhi((unsigned long long)Pf, kSixth) - (long long)mulhi((unsigned long long)SX, kThird);
-    const long long geq0 = (long long)sig - 3 * Pf - 2 * SX;                   // sigma - 3P - sigma u^2 / 2
-    const unsigned long long Om = k.Om_v;
-    long long c0 = (long long)(Om >> 1), cA = c0, cD = c0;
-    long long dq[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    if (MRT) {
-      // e and eps projections of g - g^eq from the class sums (sum_axis g^eq = P,
-      // sum_diag g^eq = P + sigma u^2 / 2), taken at 1/8 scale against overflow
-      const long long n0 = (G[0] - geq0) >> 3;
-      const long long nA = (Sa - Pf) >> 3;
-      const long long nD = (Sd - Pf - 2 * SX) >> 3;
-      const long long ae = __mul64hi(8 * nD - 11 * nA - 30 * n0, k.CE) >> 6;   // ce (M_e . (g - g^eq))
-      const long long ap = __mul64hi(nD - 4 * nA + 12 * n0, k.CP) >> 2;        // cp (M_eps . (g - g^eq))
-      c0 += 30 * ae - 12 * ap;
-      cA += 11 * ae + 4 * ap;
-      cD -= 8 * ae + ap;
-      if (QSEP) {
-        // energy-flux rows q_i = (5|c|^2 - 9) c_i, q^eq_i = -(2/3) M_i
-        const unsigned long long h23 = kTwoThirds >> 1;
-        const long long vx = ((Mx - 5 * dp[0]) >> 2) + (mulhi_su(Mx, kTwoThirds, h23) >> 2);
-        const long long vy = ((My - 5 * dp[1]) >> 2) + (mulhi_su(My, kTwoThirds, h23) >> 2);
-        const long long vz = ((Mz - 5 * dp[2]) >> 2) + (mulhi_su(Mz, kTwoThirds, h23) >> 2);
-        const long long aqx = __mul64hi(vx, k.CQ) >> 1, aqy = __mul64hi(vy, k.CQ) >> 1, aqz = __mul64hi(vz, k.CQ) >> 1;
-        dq[0] = 4 * aqx; dq[1] = 4 * aqy; dq[2] = 4 * aqz;
-        dq[3] = -(aqx + aqy); dq[4] = -(aqx - aqy);
-        dq[5] = -(aqx + aqz); dq[6] = -(aqx - aqz);
-        dq[7] = -(aqy + aqz); dq[8] = -(aqy - aqz);
-      }
+// g relaxation: Eq. 6 (BGK) or Eq. 35 (MRT as BGK plus the e, eps, q projections)
+// with the equilibria of Eqs. 8-9, written to g as FP64.
+template <bool MRT, bool QSEP>
+__device__ __forceinline__ void fx_g_relax(const GState& s, const UFix& u, const StepConst& k, double (&g)[19]) {
+  using namespace fx;
+  EqPieces q;
+  eq_pieces(s.sig, u, q);
+  const long long SX = q.Xx + q.Xy + q.Xz;                                     // sigma u^2 / 4
+  q.KA = (long long)mulhi((unsigned long long)s.Pf, kSixth) - (long long)mulhi((unsigned long long)SX, kThird);
+  const long long geq0 = (long long)s.sig - 3 * s.Pf - 2 * SX;                 // sigma - 3P - sigma u^2 / 2
+  const unsigned long long Om = k.Om_v;
+  long long c0 = (long long)(Om >> 1), cA = c0, cD = c0;
+  long long dq[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  if (MRT) {
+    // e and eps projections of g - g^eq from the class sums (sum_axis g^eq = P,
+    // sum_diag g^eq = P + sigma u^2 / 2), taken at 1/8 scale against overflow
+    const long long n0 = (s.G[0] - geq0) >> 3;
+    const long long nA = (s.Sa - s.Pf) >> 3;
+    const long long nD = (s.Sd - s.Pf - 2 * SX) >> 3;
+    const long long ae = __mul64hi(8 * nD - 11 * nA - 30 * n0, k.CE) >> 6;      // ce (M_e . (g - g^eq))
+    const long long ap = __mul64hi(nD - 4 * nA + 12 * n0, k.CP) >> 2;           // cp (M_eps . (g - g^eq))
+    c0 += 30 * ae - 12 * ap;
+    cA += 11 * ae + 4 * ap;
+    cD -= 8 * ae + ap;
+    if (QSEP) {
+      // energy-flux rows q_i = (5|c|^2 - 9) c_i, q^eq_i = -(2/3) M_i
+      const unsigned long long h23 = kTwoThirds >> 1;
+      const long long vx = ((s.Mx - 5 * s.dp[0]) >> 2) + (mulhi_su(s.Mx, kTwoThirds, h23) >> 2);
+      const long long vy = ((s.My - 5 * s.dp[1]) >> 2) + (mulhi_su(s.My, kTwoThirds, h23) >> 2);
+      const long long vz = ((s.Mz - 5 * s.dp[2]) >> 2) + (mulhi_su(s.Mz, kTwoThirds, h23) >> 2);
+      const long long aqx = __mul64hi(vx, k.CQ) >> 1, aqy = __mul64hi(vy, k.CQ) >> 1, aqz = __mul64hi(vz, k.CQ) >> 1;
+      dq[0] = 4 * aqx; dq[1] = 4 * aqy; dq[2] = 4 * aqz;
+      dq[3] = -(aqx + aqy); dq[4] = -(aqx - aqy);
+      dq[5] = -(aqx + aqz); dq[6] = -(aqx - aqz);
+      dq[7] = -(aqy + aqz); dq[8] = -(aqy - aqz);
     }
-    g[0] = from_fixed<RLB_FX_OUT_G>(relax(G[0], geq0, Om, c0), Eg);
-    relax_links<RLB_FX_OUT_G, MRT && QSEP>(G, q, Om, cA, cD, dq, Eg, g);
   }
-  // ---- f (Eq. 5 with Eq. 7)
-  {
-    EqPieces q;
-    const unsigned long long n0u = (unsigned long long)N0;
-    eq_pieces(n0u, u, q);
-    const long long SX = q.Xx + q.Xy + q.Xz;                                  // N0 u^2 / 4
-    q.KA = (long long)mulhi(n0u, kEighteenth) - (long long)mulhi((unsigned long long)SX, kThird);
-    const long long feq0 = (long long)mulhi(n0u, kThird) - 2 * SX;            // N0/3 - N0 u^2 / 2
-    const unsigned long long Om = k.Om_f;
-    const long long c = (long long)(Om >> 1);
-    f[0] = from_fixed<RLB_FX_OUT_F>(relax(F[0], feq0, Om, c), Ef);
-    relax_links<RLB_FX_OUT_F, false>(F, q, Om, c, c, dq0, Ef, f);
-  }
-  return bad;
+  g[0] = from_fixed<RLB_FX_OUT_G>(relax(s.G[0], geq0, Om, c0), s.Eg);
+  relax_links<RLB_FX_OUT_G, MRT && QSEP>(s.G, q, Om, cA, cD, dq, s.Eg, g);
+}
+
+// f half: block exponent, fixed-point values and N0 (Eq. 10, exact on the grid).
+struct FState {
+  long long F[19];
+  long long N0;
+  int Ef;
+};
+__device__ __forceinline__ void fx_f_load(const double (&f)[19], FState& s) {
+  using namespace fx;
+  unsigned mf = 0;
+#pragma unroll
+  for (int a = 0; a < 19; ++a) mf = max(mf, (unsigned)__double2hiint(f[a]) & 0x7ff00000u);
+  s.Ef = (int)(mf >> 20);
+#pragma unroll
+  for (int a = 0; a < 19; ++a) s.F[a] = to_fixed(f[a], s.Ef + 7);
+  s.N0 = s.F[0];
+#pragma unroll
+  for (int a = 1; a < 19; ++a) s.N0 += s.F[a];
+}
+__device__ __forceinline__ bool fx_f_bad(const FState& s) { return (s.Ef < 64) | (s.Ef > 2046); }
+
+// f relaxation: Eq. 5 with the equilibrium of Eq. 7, written to f as FP64.
+__device__ __forceinline__ void fx_f_relax(const FState& s, const UFix& u, const StepConst& k, double (&f)[19]) {
+  using namespace fx;
+  EqPieces q;
+  const unsigned long long n0u = (unsigned long long)s.N0;
+  eq_pieces(n0u, u, q);
+  const long long SX = q.Xx + q.Xy + q.Xz;                                     // N0 u^2 / 4
+  q.KA = (long long)mulhi(n0u, kEighteenth) - (long long)mulhi((unsigned long long)SX, kThird);
+  const long long feq0 = (long long)mulhi(n0u, kThird) - 2 * SX;               // N0/3 - N0 u^2 / 2
+  const unsigned long long Om = k.Om_f;
+  const long long c = (long long)(Om >> 1);
+  const long long dq0[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  f[0] = from_fixed<RLB_FX_OUT_F>(relax(s.F[0], feq0, Om, c), s.Ef);
+  relax_links<RLB_FX_OUT_F, false>(s.F, q, Om, c, c, dq0, s.Ef, f);
+}
+
+// FP64 node collide on the integer pipe: moments, recovery (FP64), equilibria, BGK f,
+// BGK / MRT g.  Same contract as node_collide_f64 with constant relaxation times; each
+// link agrees with it to a few units of 2^-56 of the node's largest population.
+template <bool MRT, bool QSEP>
+__device__ __forceinline__ bool node_collide_fx(double (&f)[19], double (&g)[19], const StepConst& k) {
+  GState gs;
+  FState fs;
+  UFix u;
+  fx_g_recover(g, gs, u);
+  fx_f_load(f, fs);
+  fx_g_relax<MRT, QSEP>(gs, u, k, g);
+  fx_f_relax(fs, u, k, f);
+  return gs.bad | fx_f_bad(fs);
 }
 
 // ----------------------------------------------------------------------------
