@@ -83,9 +83,13 @@ __device__ __forceinline__ void pull19(const S* __restrict__ base, unsigned long
 #ifndef RLB_F64_BLOCKS_PER_SM
 #define RLB_F64_BLOCKS_PER_SM 3
 #endif
+// and the FP32-storage step
+#ifndef RLB_F32_BLOCKS_PER_SM
+#define RLB_F32_BLOCKS_PER_SM 5
+#endif
 
 template <typename S, bool MRT, bool QSEP, bool ETA = false>
-__global__ void __launch_bounds__(kBlockX, sizeof(S) == 8 ? RLB_F64_BLOCKS_PER_SM : 1) k_step(const S* __restrict__ src, S* __restrict__ dst, Geo geo,
+__global__ void __launch_bounds__(kBlockX, sizeof(S) == 8 ? RLB_F64_BLOCKS_PER_SM : RLB_F32_BLOCKS_PER_SM) k_step(const S* __restrict__ src, S* __restrict__ dst, Geo geo,
                                                   StepConst k, unsigned long long* __restrict__ bad) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= geo.nx) return;
@@ -125,6 +129,10 @@ __global__ void __launch_bounds__(kBlockX, sizeof(S) == 8 ? RLB_F64_BLOCKS_PER_S
 // clamped node, pass the barrier and store nothing.
 #ifndef RLB_WS_BLOCKS_PER_SM
 #define RLB_WS_BLOCKS_PER_SM 5
+#endif
+// warps per role in the blocks of large lattices
+#ifndef RLB_WS_WARPS
+#define RLB_WS_WARPS 2
 #endif
 
 template <int W, bool MRT, bool QSEP>
@@ -257,13 +265,18 @@ __global__ void __launch_bounds__(64 * W, RLB_WS_BLOCKS_PER_SM * 2 / W)
       dq[7] = -(aqy + aqz); dq[8] = -(aqy - aqz);
     }
   }
-  v[0] = from_fixed<RLB_FX_OUT_G>(relax(X[0], eq0, Om, c0), E);
-  relax_links<RLB_FX_OUT_G, MRT && QSEP>(X, q, Om, cA, cD, dq, E, v);
-  if (!valid) return;
   const unsigned node = row[1][1] + (unsigned)x;
-  if (b) atomicMin(bad, (unsigned long long)node);
-#pragma unroll
-  for (int a = 0; a < 19; ++a) dst[plane0 + (unsigned long long)a * geo.plane + node] = v[a];
+  if (valid && b) atomicMin(bad, (unsigned long long)node);
+  double* out = dst + plane0 + node;
+  if (is_g) {
+    const double r0 = from_fixed<(RLB_FX_OUT_G >> 9) & 1>(relax(X[0], eq0, Om, c0), E);
+    if (valid) out[0] = r0;
+    relax_links_store<RLB_FX_OUT_G, MRT && QSEP>(X, q, Om, cA, cD, dq, E, out, geo.plane, valid);
+  } else {
+    const double r0 = from_fixed<(RLB_FX_OUT_F >> 9) & 1>(relax(X[0], eq0, Om, c0), E);
+    if (valid) out[0] = r0;
+    relax_links_store<RLB_FX_OUT_F, false>(X, q, Om, cA, cD, dq, E, out, geo.plane, valid);
+  }
 }
 
 // D2Q9 pull of the 9 f and 9 g arriving at node (x, y).
@@ -449,10 +462,11 @@ cudaError_t launch_step(rlb_handle* h, const void* src, void* dst, cudaStream_t 
       else if (!q) k_step_ws<1, true, false><<<gw, 64, 0, st>>>(s8, d8, geo, h->k, h->d_bad);
       else k_step_ws<1, true, true><<<gw, 64, 0, st>>>(s8, d8, geo, h->k, h->d_bad);
     } else {
-      dim3 gw((geo.nx + 63) / 64, geo.ny, geo.nz);
-      if (!mrt) k_step_ws<2, false, false><<<gw, 128, 0, st>>>(s8, d8, geo, h->k, h->d_bad);
-      else if (!q) k_step_ws<2, true, false><<<gw, 128, 0, st>>>(s8, d8, geo, h->k, h->d_bad);
-      else k_step_ws<2, true, true><<<gw, 128, 0, st>>>(s8, d8, geo, h->k, h->d_bad);
+      constexpr int W = RLB_WS_WARPS;
+      dim3 gw((geo.nx + 32 * W - 1) / (32 * W), geo.ny, geo.nz);
+      if (!mrt) k_step_ws<W, false, false><<<gw, 64 * W, 0, st>>>(s8, d8, geo, h->k, h->d_bad);
+      else if (!q) k_step_ws<W, true, false><<<gw, 64 * W, 0, st>>>(s8, d8, geo, h->k, h->d_bad);
+      else k_step_ws<W, true, true><<<gw, 64 * W, 0, st>>>(s8, d8, geo, h->k, h->d_bad);
     }
     return cudaGetLastError();
   } else {

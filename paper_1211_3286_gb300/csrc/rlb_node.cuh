@@ -469,12 +469,13 @@ __device__ __forceinline__ bool node_collide_f64(double (&f)[19], double (&g)[19
 //
 // Output rounding to FP64 has two routes: integer bit assembly (ALU pipe) or
 // __ll2double_rn (FP64 pipe).  RLB_FX_OUT_F / RLB_FX_OUT_G pick the route for the
-// f and g outputs (0 = integer, 1 = FP64 pipe) to balance the two pipes.
+// f and g outputs, one bit per link pair and bit 9 for the rest link (set = FP64
+// pipe), to balance the two pipes.
 #ifndef RLB_FX_OUT_F
-#define RLB_FX_OUT_F 1
+#define RLB_FX_OUT_F 0x3ff
 #endif
 #ifndef RLB_FX_OUT_G
-#define RLB_FX_OUT_G 1
+#define RLB_FX_OUT_G 0x3ff
 #endif
 
 namespace fx {
@@ -576,6 +577,8 @@ __device__ __forceinline__ void eq_pieces(unsigned long long D, const UFix& u, E
 
 // Relax the 18 moving links of one distribution: class constants cA (axis) and cD
 // (diagonal) hold Om / 2 plus any MRT class correction, dq the odd corrections.
+// DP selects the rounding route per link pair: bit p set = FP64 pipe for pair p
+// (0 = all integer, 0x1ff = all FP64 pipe).
 template <int DP, bool ODD>
 __device__ __forceinline__ void relax_links(const long long (&X)[19], const EqPieces& q, unsigned long long Om,
                                             long long cA, long long cD, const long long (&dq)[9], int E,
@@ -591,11 +594,43 @@ __device__ __forceinline__ void relax_links(const long long (&X)[19], const EqPi
   for (int p = 0; p < 9; ++p) {
     const long long c = p < 3 ? cA : cD;
     const long long d = ODD ? dq[p] : 0;
-    out[2 * p + 1] = from_fixed<DP>(relax(X[2 * p + 1], ev[p] + od[p], Om, c + d), E);
-    out[2 * p + 2] = from_fixed<DP>(relax(X[2 * p + 2], ev[p] - od[p], Om, c - d), E);
+    const long long ya = relax(X[2 * p + 1], ev[p] + od[p], Om, c + d);
+    const long long yb = relax(X[2 * p + 2], ev[p] - od[p], Om, c - d);
+    // (DP >> p) & 1 is a constant once the loop is unrolled
+    out[2 * p + 1] = ((DP >> p) & 1) ? from_fixed_dp(ya, E) : from_fixed_int(ya, E);
+    out[2 * p + 2] = ((DP >> p) & 1) ? from_fixed_dp(yb, E) : from_fixed_int(yb, E);
   }
 }
 
+
+// relax_links writing each link straight to out[a * stride] (when st) as soon as it is
+// rounded, so that the results do not all stay live until a final store loop.
+template <int DP, bool ODD>
+__device__ __forceinline__ void relax_links_store(const long long (&X)[19], const EqPieces& q, unsigned long long Om,
+                                                  long long cA, long long cD, const long long (&dq)[9], int E,
+                                                  double* __restrict__ out, unsigned long long stride, bool st) {
+  const long long KD = q.KA >> 1;
+  const long long ev[9] = {q.KA + q.Xx, q.KA + q.Xy, q.KA + q.Xz,
+                           KD + ((q.Xx + q.Xy) >> 1) + q.Yxy, KD + ((q.Xx + q.Xy) >> 1) - q.Yxy,
+                           KD + ((q.Xx + q.Xz) >> 1) + q.Yxz, KD + ((q.Xx + q.Xz) >> 1) - q.Yxz,
+                           KD + ((q.Xy + q.Xz) >> 1) + q.Yyz, KD + ((q.Xy + q.Xz) >> 1) - q.Yyz};
+  const long long od[9] = {q.Zx, q.Zy, q.Zz,
+                           (q.Zx + q.Zy) >> 1, (q.Zx - q.Zy) >> 1, (q.Zx + q.Zz) >> 1, (q.Zx - q.Zz) >> 1,
+                           (q.Zy + q.Zz) >> 1, (q.Zy - q.Zz) >> 1};
+#pragma unroll
+  for (int p = 0; p < 9; ++p) {
+    const long long c = p < 3 ? cA : cD;
+    const long long d = ODD ? dq[p] : 0;
+    const long long ya = relax(X[2 * p + 1], ev[p] + od[p], Om, c + d);
+    const long long yb = relax(X[2 * p + 2], ev[p] - od[p], Om, c - d);
+    const double da = ((DP >> p) & 1) ? from_fixed_dp(ya, E) : from_fixed_int(ya, E);
+    const double db = ((DP >> p) & 1) ? from_fixed_dp(yb, E) : from_fixed_int(yb, E);
+    if (st) {
+      out[(2 * p + 1) * stride] = da;
+      out[(2 * p + 2) * stride] = db;
+    }
+  }
+}
 }  // namespace fx
 
 using fx::EqPieces;
@@ -707,7 +742,7 @@ __device__ __forceinline__ void fx_g_relax(const GState& s, const UFix& u, const
       dq[7] = -(aqy + aqz); dq[8] = -(aqy - aqz);
     }
   }
-  g[0] = from_fixed<RLB_FX_OUT_G>(relax(s.G[0], geq0, Om, c0), s.Eg);
+  g[0] = from_fixed<(RLB_FX_OUT_G >> 9) & 1>(relax(s.G[0], geq0, Om, c0), s.Eg);
   relax_links<RLB_FX_OUT_G, MRT && QSEP>(s.G, q, Om, cA, cD, dq, s.Eg, g);
 }
 
@@ -743,7 +778,7 @@ __device__ __forceinline__ void fx_f_relax(const FState& s, const UFix& u, const
   const unsigned long long Om = k.Om_f;
   const long long c = (long long)(Om >> 1);
   const long long dq0[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-  f[0] = from_fixed<RLB_FX_OUT_F>(relax(s.F[0], feq0, Om, c), s.Ef);
+  f[0] = from_fixed<(RLB_FX_OUT_F >> 9) & 1>(relax(s.F[0], feq0, Om, c), s.Ef);
   relax_links<RLB_FX_OUT_F, false>(s.F, q, Om, c, c, dq0, s.Ef, f);
 }
 
@@ -884,13 +919,15 @@ __device__ __forceinline__ bool node_collide_f32s(float (&f)[19], float (&g)[19]
   float N0p[3];
   const int Eg = exact_sums_g(g, S);
   const int Ef = exact_sum_f(f, N0p);
-  // exact sums as integers K * 2^(E - 183); the recovery is homogeneous of degree 1
-  // in (T00, M) (u is scale free), so it runs on the unscaled K and scales after
-  const double Tu = __ll2double_rn(levels_to_int(S.T00, Eg));
-  const double Mxu = __ll2double_rn(levels_to_int(S.Mx, Eg));
-  const double Myu = __ll2double_rn(levels_to_int(S.My, Eg));
-  const double Mzu = __ll2double_rn(levels_to_int(S.Mz, Eg));
-  const double N0u = __ll2double_rn(levels_to_int(N0p, Ef));
+  // exact sums as integers K * 2^(E - 183), rounded once to FP64 by integer bit
+  // assembly (fx::from_fixed_int with unit scale: no FP64-pipe conversion); the
+  // recovery is homogeneous of degree 1 in (T00, M) (u is scale free), so it runs on
+  // the unscaled K and scales after
+  const double Tu = fx::from_fixed_int(levels_to_int(S.T00, Eg), 1079);
+  const double Mxu = fx::from_fixed_int(levels_to_int(S.Mx, Eg), 1079);
+  const double Myu = fx::from_fixed_int(levels_to_int(S.My, Eg), 1079);
+  const double Mzu = fx::from_fixed_int(levels_to_int(S.Mz, Eg), 1079);
+  const double N0u = fx::from_fixed_int(levels_to_int(N0p, Ef), 1079);
   NodeMacro m;
   const double MM = fma(Mxu, Mxu, fma(Myu, Myu, Mzu * Mzu));
   const double A = fma(scale_pow2(Tu, 2), Tu, -3.0 * MM);
@@ -900,12 +937,10 @@ __device__ __forceinline__ bool node_collide_f32s(float (&f)[19], float (&g)[19]
   m.uy = Myu * is;
   m.uz = Mzu * is;
   const double Pu = sgu - Tu;
-  m.u2 = MM * is * is;
-  m.bad = !(pos_finite_hi(A) && pos_finite_hi(Tu) && pos_finite_hi(Pu) &&
-            (unsigned)__double2hiint(m.u2) < 0x3ff00000u) || Eg == 255 || Ef == 255;
   const int eg = Eg - 183, ef = Ef - 183;
-  // per-node equilibrium constants (they cancel, sigma ~ 4P): FP64, then one rounding
-  const double su2u = sgu * m.u2;
+  // per-node equilibrium constants (they cancel, sigma ~ 4P): FP64, then one rounding;
+  // sigma u^2 = |M|^2 / sigma
+  const double su2u = MM * is;
   const double P3u = 3.0 * Pu;
   const float su2 = d2f_rn_bits(scale_pow2(su2u, eg));
   const float kg = d2f_rn_bits(scale_pow2(fma(-1.5, su2u, P3u), eg));
@@ -919,6 +954,8 @@ __device__ __forceinline__ bool node_collide_f32s(float (&f)[19], float (&g)[19]
     m.Mz = scale_pow2(Mzu, eg);
   }
   const float u2 = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
+  // A > 0, T00 > 0, P > 0 (all finite), u^2 < 1 (on the rounded velocity; NaN fails)
+  m.bad = !(pos_finite_hi(A) && pos_finite_hi(Tu) && pos_finite_hi(Pu) && u2 < 1.0f) || Eg == 255 || Ef == 255;
   float cu[9];
   pair_cu<float>(ux, uy, uz, cu);
   {
