@@ -130,6 +130,15 @@ __global__ void __launch_bounds__(kBlockX, sizeof(S) == 8 ? RLB_F64_BLOCKS_PER_S
 #ifndef RLB_WS_BLOCKS_PER_SM
 #define RLB_WS_BLOCKS_PER_SM 5
 #endif
+// Output rounding route of the f and g warps, one bit per link pair and bit 9 for
+// the rest link: set = FP64-pipe conversion, clear = integer bit assembly with the
+// FP64 pipe only for negative or tiny values (fx::from_fixed_pos).
+#ifndef RLB_WS_OUT_F
+#define RLB_WS_OUT_F 0x3ff
+#endif
+#ifndef RLB_WS_OUT_G
+#define RLB_WS_OUT_G 0x3ff
+#endif
 // warps per role in the blocks of large lattices
 #ifndef RLB_WS_WARPS
 #define RLB_WS_WARPS 2
@@ -161,14 +170,31 @@ __global__ void __launch_bounds__(64 * W, RLB_WS_BLOCKS_PER_SM * 2 / W)
   pull19<double>(src + plane0, geo.plane, xs, row, v);
 
   using namespace fx;
-  // both roles: block exponent and fixed-point values
-  unsigned me = 0;
+  // both roles: block exponent and fixed-point values.  When every value of every
+  // lane of the warp is positive, finite and within 2^24 of its node's largest (the
+  // normal case), the conversion skips the sign and the long-shift handling.
+  int hmax = __double2hiint(v[0]), hmin = hmax;
 #pragma unroll
-  for (int a = 0; a < 19; ++a) me = max(me, (unsigned)__double2hiint(v[a]) & 0x7ff00000u);
-  const int E = (int)(me >> 20);
+  for (int a = 1; a < 19; ++a) {
+    const int h = __double2hiint(v[a]);
+    hmax = max(hmax, h);
+    hmin = min(hmin, h);
+  }
+  const bool fast = __all_sync(0xffffffffu, hmin > 0 && hmax < 0x7ff00000 && hmin >= (((hmax >> 20) - 24) << 20));
+  int E;
   long long X[19];
+  if (fast) {
+    E = hmax >> 20;
 #pragma unroll
-  for (int a = 0; a < 19; ++a) X[a] = to_fixed(v[a], E + 7);
+    for (int a = 0; a < 19; ++a) X[a] = to_fixed_pos(v[a], E + 7);
+  } else {
+    unsigned me = 0;
+#pragma unroll
+    for (int a = 0; a < 19; ++a) me = max(me, (unsigned)__double2hiint(v[a]) & 0x7ff00000u);
+    E = (int)(me >> 20);
+#pragma unroll
+    for (int a = 0; a < 19; ++a) X[a] = to_fixed(v[a], E + 7);
+  }
 
   UFix u;
   long long Sa = 0, Sd = 0, T00 = 0, Mx = 0, My = 0, Mz = 0, Pf = 0, dp0 = 0, dp1 = 0, dp2 = 0, N0 = 0;
@@ -269,13 +295,13 @@ __global__ void __launch_bounds__(64 * W, RLB_WS_BLOCKS_PER_SM * 2 / W)
   if (valid && b) atomicMin(bad, (unsigned long long)node);
   double* out = dst + plane0 + node;
   if (is_g) {
-    const double r0 = from_fixed<(RLB_FX_OUT_G >> 9) & 1>(relax(X[0], eq0, Om, c0), E);
+    const double r0 = from_fixed<(RLB_WS_OUT_G >> 9) & 1>(relax(X[0], eq0, Om, c0), E);
     if (valid) out[0] = r0;
-    relax_links_store<RLB_FX_OUT_G, MRT && QSEP>(X, q, Om, cA, cD, dq, E, out, geo.plane, valid);
+    relax_links_store<RLB_WS_OUT_G, MRT && QSEP>(X, q, Om, cA, cD, dq, E, out, geo.plane, valid);
   } else {
-    const double r0 = from_fixed<(RLB_FX_OUT_F >> 9) & 1>(relax(X[0], eq0, Om, c0), E);
+    const double r0 = from_fixed<(RLB_WS_OUT_F >> 9) & 1>(relax(X[0], eq0, Om, c0), E);
     if (valid) out[0] = r0;
-    relax_links_store<RLB_FX_OUT_F, false>(X, q, Om, cA, cD, dq, E, out, geo.plane, valid);
+    relax_links_store<RLB_WS_OUT_F, false>(X, q, Om, cA, cD, dq, E, out, geo.plane, valid);
   }
 }
 

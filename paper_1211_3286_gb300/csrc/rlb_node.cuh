@@ -467,8 +467,8 @@ __device__ __forceinline__ bool node_collide_f64(double (&f)[19], double (&g)[19
 // few grid units; only the recovery (Eq. 10 inverted) runs in FP64.  Each output
 // is rounded once to FP64.
 //
-// Output rounding to FP64 has two routes: integer bit assembly (ALU pipe) or
-// __ll2double_rn (FP64 pipe).  RLB_FX_OUT_F / RLB_FX_OUT_G pick the route for the
+// Output rounding to FP64 has two routes: integer bit assembly (ALU pipe; the FP64
+// pipe only for negative or tiny values) or __ll2double_rn (FP64 pipe).  RLB_FX_OUT_F / RLB_FX_OUT_G pick the route for the
 // f and g outputs, one bit per link pair and bit 9 for the rest link (set = FP64
 // pipe), to balance the two pipes.
 #ifndef RLB_FX_OUT_F
@@ -529,16 +529,41 @@ __device__ __forceinline__ double from_fixed_int(long long K, int E) {
   const unsigned long long bits = m + ((unsigned long long)(unsigned)(E + 6 - lz) << 52) + (s << 63);
   return a ? __longlong_as_double((long long)bits) : 0.0;
 }
+// Fast form of to_fixed for a positive normal x whose biased exponent lies within
+// [Er - 31, Er] (no sign, no long shift).
+__device__ __forceinline__ long long to_fixed_pos(double x, int Er) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned r = (unsigned)(Er - (int)(hi >> 20));
+  const unsigned th = __funnelshift_l(lo, hi, 11) | 0x80000000u;
+  const unsigned tl = lo << 11;
+  return (long long)(((unsigned long long)(th >> r) << 32) | __funnelshift_r(tl, th, r));
+}
+
 // The same through the FP64 pipe's int64 conversion (round to nearest even).
 __device__ __forceinline__ double from_fixed_dp(long long K, int E) {
   const double d = __ll2double_rn(K);
   const int hi = __double2hiint(d);
   return __hiloint2double(K ? hi + (int)((unsigned)(E - 1079) << 20) : hi, __double2loint(d));
 }
+// K * 2^(E - 1079) rounded to the nearest double (ties to even) by integer bit
+// assembly for 2^32 <= K < 2^63, the range of a population near its node's largest;
+// other K (negative, zero, tiny) take the FP64-pipe conversion.
+__device__ __forceinline__ double from_fixed_pos(long long K, int E) {
+  const unsigned hi = (unsigned)((unsigned long long)K >> 32), lo = (unsigned)K;
+  if ((hi - 1u) >= 0x7fffffffu) return from_fixed_dp(K, E);
+  const int lz = __clz(hi);                                   // 1..31
+  const unsigned nh = __funnelshift_l(lo, hi, lz), nl = lo << lz;   // K << lz, bit 63 set
+  const unsigned mh = nh >> 11, ml = __funnelshift_r(nl, nh, 11);
+  const unsigned rb = nl & 0x7ffu;                             // bits below the 53-bit significand
+  const unsigned up = (rb > 0x400u) | ((rb == 0x400u) & ml);  // round half to even
+  const unsigned long long m = (((unsigned long long)mh << 32) | ml) + up;
+  return __hiloint2double((int)((unsigned)(m >> 32) + ((unsigned)(E + 6 - lz) << 20)), (int)(unsigned)m);
+}
+
 template <int DP>
 __device__ __forceinline__ double from_fixed(long long K, int E) {
   if constexpr (DP) return from_fixed_dp(K, E);
-  else return from_fixed_int(K, E);
+  else return from_fixed_pos(K, E);
 }
 
 // One relaxation X - omega (X - X^eq) + c with Om = omega 2^63: the biased product
@@ -597,8 +622,8 @@ __device__ __forceinline__ void relax_links(const long long (&X)[19], const EqPi
     const long long ya = relax(X[2 * p + 1], ev[p] + od[p], Om, c + d);
     const long long yb = relax(X[2 * p + 2], ev[p] - od[p], Om, c - d);
     // (DP >> p) & 1 is a constant once the loop is unrolled
-    out[2 * p + 1] = ((DP >> p) & 1) ? from_fixed_dp(ya, E) : from_fixed_int(ya, E);
-    out[2 * p + 2] = ((DP >> p) & 1) ? from_fixed_dp(yb, E) : from_fixed_int(yb, E);
+    out[2 * p + 1] = ((DP >> p) & 1) ? from_fixed_dp(ya, E) : from_fixed_pos(ya, E);
+    out[2 * p + 2] = ((DP >> p) & 1) ? from_fixed_dp(yb, E) : from_fixed_pos(yb, E);
   }
 }
 
@@ -623,8 +648,8 @@ __device__ __forceinline__ void relax_links_store(const long long (&X)[19], cons
     const long long d = ODD ? dq[p] : 0;
     const long long ya = relax(X[2 * p + 1], ev[p] + od[p], Om, c + d);
     const long long yb = relax(X[2 * p + 2], ev[p] - od[p], Om, c - d);
-    const double da = ((DP >> p) & 1) ? from_fixed_dp(ya, E) : from_fixed_int(ya, E);
-    const double db = ((DP >> p) & 1) ? from_fixed_dp(yb, E) : from_fixed_int(yb, E);
+    const double da = ((DP >> p) & 1) ? from_fixed_dp(ya, E) : from_fixed_pos(ya, E);
+    const double db = ((DP >> p) & 1) ? from_fixed_dp(yb, E) : from_fixed_pos(yb, E);
     if (st) {
       out[(2 * p + 1) * stride] = da;
       out[(2 * p + 2) * stride] = db;
