@@ -937,13 +937,19 @@ __device__ __forceinline__ long long levels_to_int(const float (&v)[3], int E) {
 
 // FP32-storage node collide: the conserved sums exact (above) and delivered in
 // FP64, the recovery (sqrt, reciprocal) in FP64; equilibria, MRT projection and
-// relaxation in FP32 with one rounding on store.
+// relaxation in FP32 with one rounding on store.  Split into the g part (sums,
+// recovery, g relaxation) and the f part (N0, f relaxation), which share only u.
+struct G32 {
+  float sg, P, su2, kg, geq0;   // sigma, P, sigma u^2, 3P - 1.5 sigma u^2, g^eq_0
+  float Sa, Sd;                 // axis / diagonal class sums of g (MRT)
+  float Mx, My, Mz;             // momentum (energy-flux rows)
+  float ux, uy, uz;
+  bool bad;
+};
 template <bool MRT, bool QSEP>
-__device__ __forceinline__ bool node_collide_f32s(float (&f)[19], float (&g)[19], const StepConst& k) {
+__device__ __forceinline__ void f32s_g_recover(const float (&g)[19], G32& s) {
   Sums3 S;
-  float N0p[3];
   const int Eg = exact_sums_g(g, S);
-  const int Ef = exact_sum_f(f, N0p);
   // exact sums as integers K * 2^(E - 183), rounded once to FP64 by integer bit
   // assembly (fx::from_fixed_int with unit scale: no FP64-pipe conversion); the
   // recovery is homogeneous of degree 1 in (T00, M) (u is scale free), so it runs on
@@ -952,102 +958,126 @@ __device__ __forceinline__ bool node_collide_f32s(float (&f)[19], float (&g)[19]
   const double Mxu = fx::from_fixed_int(levels_to_int(S.Mx, Eg), 1079);
   const double Myu = fx::from_fixed_int(levels_to_int(S.My, Eg), 1079);
   const double Mzu = fx::from_fixed_int(levels_to_int(S.Mz, Eg), 1079);
-  const double N0u = fx::from_fixed_int(levels_to_int(N0p, Ef), 1079);
-  NodeMacro m;
   const double MM = fma(Mxu, Mxu, fma(Myu, Myu, Mzu * Mzu));
   const double A = fma(scale_pow2(Tu, 2), Tu, -3.0 * MM);
   const double sgu = fma(2.0, Tu, sqrt_seeded(A)) * (1.0 / 3.0);
   const double is = rcp_seeded(sgu);
-  m.ux = Mxu * is;
-  m.uy = Myu * is;
-  m.uz = Mzu * is;
   const double Pu = sgu - Tu;
-  const int eg = Eg - 183, ef = Ef - 183;
+  const int eg = Eg - 183;
   // per-node equilibrium constants (they cancel, sigma ~ 4P): FP64, then one rounding;
   // sigma u^2 = |M|^2 / sigma
   const double su2u = MM * is;
   const double P3u = 3.0 * Pu;
-  const float su2 = d2f_rn_bits(scale_pow2(su2u, eg));
-  const float kg = d2f_rn_bits(scale_pow2(fma(-1.5, su2u, P3u), eg));
-  const float geq0 = d2f_rn_bits(scale_pow2(fma(-0.5, su2u, sgu - P3u), eg));
-  const float ux = d2f_rn_bits(m.ux), uy = d2f_rn_bits(m.uy), uz = d2f_rn_bits(m.uz);
-  const float N0 = d2f_rn_bits(scale_pow2(N0u, ef)), sg = d2f_rn_bits(scale_pow2(sgu, eg));
-  const float P = d2f_rn_bits(scale_pow2(Pu, eg));
-  if (QSEP) {
-    m.Mx = scale_pow2(Mxu, eg);
-    m.My = scale_pow2(Myu, eg);
-    m.Mz = scale_pow2(Mzu, eg);
+  s.su2 = d2f_rn_bits(scale_pow2(su2u, eg));
+  s.kg = d2f_rn_bits(scale_pow2(fma(-1.5, su2u, P3u), eg));
+  s.geq0 = d2f_rn_bits(scale_pow2(fma(-0.5, su2u, sgu - P3u), eg));
+  s.ux = d2f_rn_bits(Mxu * is);
+  s.uy = d2f_rn_bits(Myu * is);
+  s.uz = d2f_rn_bits(Mzu * is);
+  s.sg = d2f_rn_bits(scale_pow2(sgu, eg));
+  s.P = d2f_rn_bits(scale_pow2(Pu, eg));
+  if (MRT) {
+    // non-equilibrium class sums in FP32 (their rounding is far below the FP32 storage rounding)
+    s.Sa = (S.Sa[0] + S.Sa[1]) + S.Sa[2];
+    s.Sd = (S.Sd[0] + S.Sd[1]) + S.Sd[2];
   }
-  const float u2 = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
+  if (QSEP) {
+    s.Mx = d2f_rn_bits(scale_pow2(Mxu, eg));
+    s.My = d2f_rn_bits(scale_pow2(Myu, eg));
+    s.Mz = d2f_rn_bits(scale_pow2(Mzu, eg));
+  }
+  const float u2 = fmaf(s.ux, s.ux, fmaf(s.uy, s.uy, s.uz * s.uz));
   // A > 0, T00 > 0, P > 0 (all finite), u^2 < 1 (on the rounded velocity; NaN fails)
-  m.bad = !(pos_finite_hi(A) && pos_finite_hi(Tu) && pos_finite_hi(Pu) && u2 < 1.0f) || Eg == 255 || Ef == 255;
+  s.bad = !(pos_finite_hi(A) && pos_finite_hi(Tu) && pos_finite_hi(Pu) && u2 < 1.0f) || Eg == 255;
+}
+
+template <bool MRT, bool QSEP>
+__device__ __forceinline__ void f32s_g_relax(float (&g)[19], const G32& s, const StepConst& k) {
+  float cu[9];
+  pair_cu<float>(s.ux, s.uy, s.uz, cu);
+  float KA = k.gA_k_f * s.kg, KD = k.gD_k_f * s.kg;
+  const float SA = k.gA_s_f * s.sg, SD = k.gD_s_f * s.sg;
+  const float AA = k.gA_a_f * s.sg, AD = k.gD_a_f * s.sg;
+  float g0n = fmaf(k.omv1_f, g[0], k.omv_f * s.geq0);
+  float dq[9];
+#pragma unroll
+  for (int p = 0; p < 9; ++p) dq[p] = 0.0f;
+  if (MRT) {
+    const float n0 = g[0] - s.geq0;
+    const float nA = s.Sa - s.P;
+    const float nD = fmaf(-0.5f, s.su2, s.Sd - s.P);
+    const float ne = fmaf(8.0f, nD, fmaf(-11.0f, nA, -30.0f * n0));
+    const float np = fmaf(-4.0f, nA, fmaf(12.0f, n0, nD));
+    const float ae = k.ce_f * ne, ap = k.cp_f * np;
+    g0n = g0n + fmaf(30.0f, ae, -12.0f * ap);
+    KA = KA + fmaf(11.0f, ae, 4.0f * ap);
+    KD = KD - fmaf(8.0f, ae, ap);
+    if (QSEP) {
+      const float qeq = -2.0f / 3.0f;
+      const float d0 = g[1] - g[2], d1 = g[3] - g[4], d2 = g[5] - g[6], d3 = g[7] - g[8], d4 = g[9] - g[10];
+      const float d5 = g[11] - g[12], d6 = g[13] - g[14], d7 = g[15] - g[16], d8 = g[17] - g[18];
+      const float qx = fmaf(-4.0f, d0, ((d3 + d4) + d5) + d6);
+      const float qy = fmaf(-4.0f, d1, ((d3 - d4) + d7) + d8);
+      const float qz = fmaf(-4.0f, d2, ((d5 - d6) + d7) - d8);
+      const float cq = k.cq_f;
+      const float aqx = cq * fmaf(-qeq, s.Mx, qx);
+      const float aqy = cq * fmaf(-qeq, s.My, qy);
+      const float aqz = cq * fmaf(-qeq, s.Mz, qz);
+      dq[0] = 4.0f * aqx; dq[1] = 4.0f * aqy; dq[2] = 4.0f * aqz;
+      dq[3] = -(aqx + aqy); dq[4] = -(aqx - aqy);
+      dq[5] = -(aqx + aqz); dq[6] = -(aqx - aqz);
+      dq[7] = -(aqy + aqz); dq[8] = -(aqy - aqz);
+    }
+  }
+  g[0] = g0n;
+#pragma unroll
+  for (int p = 0; p < 9; ++p) {
+    const bool ax = p < 3;
+    const float ev = fmaf(ax ? SA : SD, cu[p] * cu[p], ax ? KA : KD);
+    float od = (ax ? AA : AD) * cu[p];
+    if (MRT && QSEP) od += dq[p];
+    g[2 * p + 1] = fmaf(k.omv1_f, g[2 * p + 1], ev + od);
+    g[2 * p + 2] = fmaf(k.omv1_f, g[2 * p + 2], ev - od);
+  }
+}
+
+// f part: N0 (exact sum rounded to FP32 through FP64) and the flag of a non-finite f.
+__device__ __forceinline__ float f32s_f_sum(const float (&f)[19], bool& bad) {
+  float N0p[3];
+  const int Ef = exact_sum_f(f, N0p);
+  bad = Ef == 255;
+  return d2f_rn_bits(scale_pow2(fx::from_fixed_int(levels_to_int(N0p, Ef), 1079), Ef - 183));
+}
+
+__device__ __forceinline__ void f32s_f_relax(float (&f)[19], float N0, float ux, float uy, float uz,
+                                             const StepConst& k) {
+  const float u2 = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
   float cu[9];
   pair_cu<float>(ux, uy, uz, cu);
-  {
-    const float kf = fmaf(-1.5f * N0, u2, N0);
-    const float KA = k.fA_k_f * kf, KD = k.fD_k_f * kf;
-    const float SA = k.fA_s_f * N0, SD = k.fD_s_f * N0;
-    const float AA = k.fA_a_f * N0, AD = k.fD_a_f * N0;
-    f[0] = fmaf(k.omf1_f, f[0], k.f0_k_f * kf);
+  const float kf = fmaf(-1.5f * N0, u2, N0);
+  const float KA = k.fA_k_f * kf, KD = k.fD_k_f * kf;
+  const float SA = k.fA_s_f * N0, SD = k.fD_s_f * N0;
+  const float AA = k.fA_a_f * N0, AD = k.fD_a_f * N0;
+  f[0] = fmaf(k.omf1_f, f[0], k.f0_k_f * kf);
 #pragma unroll
-    for (int p = 0; p < 9; ++p) {
-      const bool ax = p < 3;
-      const float ev = fmaf(ax ? SA : SD, cu[p] * cu[p], ax ? KA : KD);
-      const float od = (ax ? AA : AD) * cu[p];
-      f[2 * p + 1] = fmaf(k.omf1_f, f[2 * p + 1], ev + od);
-      f[2 * p + 2] = fmaf(k.omf1_f, f[2 * p + 2], ev - od);
-    }
+  for (int p = 0; p < 9; ++p) {
+    const bool ax = p < 3;
+    const float ev = fmaf(ax ? SA : SD, cu[p] * cu[p], ax ? KA : KD);
+    const float od = (ax ? AA : AD) * cu[p];
+    f[2 * p + 1] = fmaf(k.omf1_f, f[2 * p + 1], ev + od);
+    f[2 * p + 2] = fmaf(k.omf1_f, f[2 * p + 2], ev - od);
   }
-  {
-    float KA = k.gA_k_f * kg, KD = k.gD_k_f * kg;
-    const float SA = k.gA_s_f * sg, SD = k.gD_s_f * sg;
-    const float AA = k.gA_a_f * sg, AD = k.gD_a_f * sg;
-    float g0n = fmaf(k.omv1_f, g[0], k.omv_f * geq0);
-    float dq[9];
-#pragma unroll
-    for (int p = 0; p < 9; ++p) dq[p] = 0.0f;
-    if (MRT) {
-      // non-equilibrium class sums in FP32 (their rounding is far below the FP32 storage rounding)
-      const float Sa = (S.Sa[0] + S.Sa[1]) + S.Sa[2];
-      const float Sd = (S.Sd[0] + S.Sd[1]) + S.Sd[2];
-      const float n0 = g[0] - geq0;
-      const float nA = Sa - P;
-      const float nD = fmaf(-0.5f, su2, Sd - P);
-      const float ne = fmaf(8.0f, nD, fmaf(-11.0f, nA, -30.0f * n0));
-      const float np = fmaf(-4.0f, nA, fmaf(12.0f, n0, nD));
-      const float ae = k.ce_f * ne, ap = k.cp_f * np;
-      g0n = g0n + fmaf(30.0f, ae, -12.0f * ap);
-      KA = KA + fmaf(11.0f, ae, 4.0f * ap);
-      KD = KD - fmaf(8.0f, ae, ap);
-      if (QSEP) {
-        const float qeq = -2.0f / 3.0f;
-        const float d0 = g[1] - g[2], d1 = g[3] - g[4], d2 = g[5] - g[6], d3 = g[7] - g[8], d4 = g[9] - g[10];
-        const float d5 = g[11] - g[12], d6 = g[13] - g[14], d7 = g[15] - g[16], d8 = g[17] - g[18];
-        const float qx = fmaf(-4.0f, d0, ((d3 + d4) + d5) + d6);
-        const float qy = fmaf(-4.0f, d1, ((d3 - d4) + d7) + d8);
-        const float qz = fmaf(-4.0f, d2, ((d5 - d6) + d7) - d8);
-        const float cq = k.cq_f;
-        const float aqx = cq * fmaf(-qeq, d2f_rn_bits(m.Mx), qx);
-        const float aqy = cq * fmaf(-qeq, d2f_rn_bits(m.My), qy);
-        const float aqz = cq * fmaf(-qeq, d2f_rn_bits(m.Mz), qz);
-        dq[0] = 4.0f * aqx; dq[1] = 4.0f * aqy; dq[2] = 4.0f * aqz;
-        dq[3] = -(aqx + aqy); dq[4] = -(aqx - aqy);
-        dq[5] = -(aqx + aqz); dq[6] = -(aqx - aqz);
-        dq[7] = -(aqy + aqz); dq[8] = -(aqy - aqz);
-      }
-    }
-    g[0] = g0n;
-#pragma unroll
-    for (int p = 0; p < 9; ++p) {
-      const bool ax = p < 3;
-      const float ev = fmaf(ax ? SA : SD, cu[p] * cu[p], ax ? KA : KD);
-      float od = (ax ? AA : AD) * cu[p];
-      if (MRT && QSEP) od += dq[p];
-      g[2 * p + 1] = fmaf(k.omv1_f, g[2 * p + 1], ev + od);
-      g[2 * p + 2] = fmaf(k.omv1_f, g[2 * p + 2], ev - od);
-    }
-  }
-  return m.bad;
+}
+
+template <bool MRT, bool QSEP>
+__device__ __forceinline__ bool node_collide_f32s(float (&f)[19], float (&g)[19], const StepConst& k) {
+  G32 s;
+  f32s_g_recover<MRT, QSEP>(g, s);
+  bool fbad;
+  const float N0 = f32s_f_sum(f, fbad);
+  f32s_f_relax(f, N0, s.ux, s.uy, s.uz, k);
+  f32s_g_relax<MRT, QSEP>(g, s, k);
+  return s.bad | fbad;
 }
 
 // Equilibrium populations of given fields (Eqs. 7-9, P = e/3), FP64.

@@ -141,6 +141,48 @@ def test_fields_round_trip_and_host_io():
     lat.close()
 
 
+@pytest.mark.parametrize("collision, tau_q", [("mrt", 0.7), ("mrt", 0.0), ("bgk", 0.0)])
+def test_general_conversion_paths_one_step(collision, tau_q):
+    """States outside the fast path of the FP64 step: negative populations, exact
+    zeros and values 1e-12 of their node's largest (the general fixed-point
+    conversion, and outputs that take the FP64-pipe rounding).  One step against
+    the oracle, per population, relative to the largest population of the lattice."""
+    from paper_1211_3286_gb300.lattice import Lattice
+    shape = (3, 4, 70)
+    e, ux, uy, uz, n = I.periodic_box(None, seed=27, shape=shape)
+    f, g = O.init_populations(e, torch.stack([ux, uy, uz]), n)
+    rng = np.random.default_rng(7)
+    flat = np.arange(e.numel())
+    g = g.reshape(19, -1).clone()
+    f = f.reshape(19, -1).clone()
+    neg = rng.choice(flat, 40, replace=False)
+    g[3, neg] = -0.05 * g[3, neg]                 # negative populations
+    g[12, neg[:10]] = -0.02 * g[12, neg[:10]]
+    tiny = rng.choice(flat, 40, replace=False)
+    f[5, tiny] = 1e-12 * f[5, tiny]               # 2^-40 of the node's largest
+    g[9, tiny[:20]] = 1e-12 * g[9, tiny[:20]]
+    zero = rng.choice(flat, 20, replace=False)
+    g[8, zero] = 0.0
+    f[14, zero] = 0.0
+    big = rng.choice(flat, 40, replace=False)     # far from equilibrium: over-relaxed outputs turn negative
+    g[4, big] = 3.0 * g[4, big]
+    f[6, big] = 3.0 * f[6, big]
+    f, g = f.reshape(19, *shape), g.reshape(19, *shape)
+    taus = dict(tau_f=0.52, tau_v=0.52, tau_e=0.55, tau_eps=0.8, tau_q=tau_q)
+    lat = Lattice(shape, collision=collision, **taus)
+    lat.load_state(torch.cat([f, g]).cuda())
+    lat.step(1)
+    lat.check()
+    got = lat.state("cpu")
+    lat.close()
+    prm = O.Params(collision=collision, **taus)
+    fr, gr = O.step(f, g, prm, check=False)
+    assert float(gr.min()) < 0 and float(fr.min()) < 0     # the negative-output path ran
+    for a, b in ((got[:19], fr), (got[19:], gr)):
+        err = float((a - b).abs().max() / b.abs().max())
+        assert err < 1e-13, err
+
+
 def test_invalid_fields_are_rejected():
     from paper_1211_3286_gb300 import _lib as L
     from paper_1211_3286_gb300.lattice import Lattice
