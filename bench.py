@@ -60,6 +60,13 @@ WORKLOADS = {
 }
 TAUS = dict(tau_f=0.9, tau_v=0.9, tau_e=0.55, tau_eps=0.8)
 
+# DRAM bytes (read + write) per node update of the step kernel, from ncu captures of the
+# 128^3 box with the same kernel (the 256^3 / 512^3 lattices exceed the capture size
+# rule); traffic per launch = bytes per update x nodes.  profiles/k_step_ws_box128_f64.md:
+# 1227.8 MB / 2,097,152; profiles/k_step_box128_f32.md: 588.6 MB / 2,097,152.  None
+# where the kernel changed since its capture.
+NCU_BYTES_PER_UPDATE = {"fp64": 1227.780864e6 / 2097152, "fp32": None}
+
 # FP64-pipe operations of one FP32-storage node update (the sums are exact on the
 # FP32 and integer pipes and rounded to FP64 by integer bit assembly): recovery 20
 # (|M|^2 3, A 2, sqrt 6, sigma 2, reciprocal 3, u 3, P 1) + sigma u^2 1 +
@@ -414,8 +421,10 @@ def run_ours(args):
 
     hbm_peak, peak_kind = _peaks()
     gbs = wl["bytes_per_update"] * nodes / per_launch_s / 1e9
+    nb = NCU_BYTES_PER_UPDATE.get(wl["precision"])
+    traffic = None if nb is None else nb * nodes
     hbm = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
-           "traffic": None, "peak_kind": peak_kind}
+           "traffic": traffic, "peak_kind": peak_kind}
     roof = hbm
     if wl["precision"] == "fp64":
         # The FP64 pipe (152 SMs x 2 instructions per clock x 2.07 GHz) carries the
@@ -424,7 +433,7 @@ def run_ours(args):
         fp64_peak = 152 * 2 * 2.07
         gops = FP64_OPS_PER_UPDATE * nodes / per_launch_s / 1e9
         alu = {"bound": "alu", "achieved": gops, "peak": fp64_peak, "unit": "G FP64-pipe op/s",
-               "frac": gops / fp64_peak, "traffic": None,
+               "frac": gops / fp64_peak, "traffic": traffic,
                "peak_kind": "derived: 152 SM x 2 FP64 op/clk x 2.07 GHz (measured 2.05 DFMA/clk/SM)",
                "hbm_frac": gbs / hbm_peak}
         if alu["frac"] > hbm["frac"]:

@@ -853,6 +853,14 @@ __device__ __forceinline__ int max_exp19(const float (&p)[19]) {
   return (int)(m >> 23);
 }
 
+// Smallest biased exponent of |p| over the 19 values (0 if any is zero or subnormal).
+__device__ __forceinline__ int min_exp19(const float (&p)[19]) {
+  unsigned m = __float_as_uint(p[0]) & 0x7fffffffu;
+#pragma unroll
+  for (int a = 1; a < 19; ++a) m = min(m, __float_as_uint(p[a]) & 0x7fffffffu);
+  return (int)(m >> 23);
+}
+
 // Widen an FP32 value to FP64 by moving its bits (exact; no FP64-pipe conversion).
 __device__ __forceinline__ double f2d_bits(float x) {
   const unsigned b = __float_as_uint(x);
@@ -866,15 +874,21 @@ __device__ __forceinline__ double sum3_to_f64(const float (&v)[3]) {
   return (f2d_bits(v[0]) + f2d_bits(v[1])) + f2d_bits(v[2]);
 }
 
-// Exact level sums of g: T00, M, and the axis / diagonal class sums.
-__device__ __forceinline__ int exact_sums_g(const float (&g)[19], Sums3& S) {
-  const int E = max_exp19(g);
+// Exact level sums of g: T00, M, and the axis / diagonal class sums.  LV levels
+// (3 in general; 2 suffice when every value lies within 2^13 of the largest, since
+// the third level's parts are then all zero); parts of unused levels are 0.
+template <int LV>
+__device__ __forceinline__ void exact_sums_g(const float (&g)[19], int E, Sums3& S) {
   const float sg[3] = {pow2_bits(E + 6), pow2_bits(E - 13), pow2_bits(E - 32)};
   float r[19];
 #pragma unroll
   for (int a = 0; a < 19; ++a) r[a] = g[a];
 #pragma unroll
   for (int L = 0; L < 3; ++L) {
+    if (L >= LV) {
+      S.Sa[L] = S.Sd[L] = S.T00[L] = S.Mx[L] = S.My[L] = S.Mz[L] = 0.0f;
+      continue;
+    }
     float q[19];
 #pragma unroll
     for (int a = 0; a < 19; ++a) {
@@ -893,17 +907,20 @@ __device__ __forceinline__ int exact_sums_g(const float (&g)[19], Sums3& S) {
     S.My[L] = ((d[1] + d[3]) - (d[4] - d[7])) + d[8];
     S.Mz[L] = ((d[2] + d[5]) - (d[6] - d[7])) - d[8];
   }
-  return E;
 }
 
-__device__ __forceinline__ int exact_sum_f(const float (&f)[19], float (&N0)[3]) {
-  const int E = max_exp19(f);
+template <int LV>
+__device__ __forceinline__ void exact_sum_f(const float (&f)[19], int E, float (&N0)[3]) {
   const float sg[3] = {pow2_bits(E + 6), pow2_bits(E - 13), pow2_bits(E - 32)};
   float r[19];
 #pragma unroll
   for (int a = 0; a < 19; ++a) r[a] = f[a];
 #pragma unroll
   for (int L = 0; L < 3; ++L) {
+    if (L >= LV) {
+      N0[L] = 0.0f;
+      continue;
+    }
     float q[19];
 #pragma unroll
     for (int a = 0; a < 19; ++a) {
@@ -915,7 +932,6 @@ __device__ __forceinline__ int exact_sum_f(const float (&f)[19], float (&N0)[3])
              (((q[8] + q[9]) + (q[10] + q[11])) + ((q[12] + q[13]) + (q[14] + q[15])))) +
             ((q[16] + q[17]) + q[18]);
   }
-  return E;
 }
 
 // The three level sums of one extraction are integer multiples of their grids
@@ -931,8 +947,10 @@ __device__ __forceinline__ long long level_int(float v, int eg) {
   const long long k = es == 0 ? 0 : (long long)(m >> sh);
   return (b >> 31) ? -k : k;
 }
+template <int LV = 3>
 __device__ __forceinline__ long long levels_to_int(const float (&v)[3], int E) {
-  return (level_int(v[0], E - 18) << 38) + (level_int(v[1], E - 37) << 19) + level_int(v[2], E - 56);
+  const long long k12 = (level_int(v[0], E - 18) << 38) + (level_int(v[1], E - 37) << 19);
+  return LV > 2 ? k12 + level_int(v[2], E - 56) : k12;
 }
 
 // FP32-storage node collide: the conserved sums exact (above) and delivered in
@@ -949,15 +967,29 @@ struct G32 {
 template <bool MRT, bool QSEP>
 __device__ __forceinline__ void f32s_g_recover(const float (&g)[19], G32& s) {
   Sums3 S;
-  const int Eg = exact_sums_g(g, S);
+  const int Eg = max_exp19(g);
   // exact sums as integers K * 2^(E - 183), rounded once to FP64 by integer bit
   // assembly (fx::from_fixed_int with unit scale: no FP64-pipe conversion); the
   // recovery is homogeneous of degree 1 in (T00, M) (u is scale free), so it runs on
   // the unscaled K and scales after
-  const double Tu = fx::from_fixed_int(levels_to_int(S.T00, Eg), 1079);
-  const double Mxu = fx::from_fixed_int(levels_to_int(S.Mx, Eg), 1079);
-  const double Myu = fx::from_fixed_int(levels_to_int(S.My, Eg), 1079);
-  const double Mzu = fx::from_fixed_int(levels_to_int(S.Mz, Eg), 1079);
+  long long KT, KX, KY, KZ;
+  if (min_exp19(g) >= Eg - 13) {   // two extraction levels are exact
+    exact_sums_g<2>(g, Eg, S);
+    KT = levels_to_int<2>(S.T00, Eg);
+    KX = levels_to_int<2>(S.Mx, Eg);
+    KY = levels_to_int<2>(S.My, Eg);
+    KZ = levels_to_int<2>(S.Mz, Eg);
+  } else {
+    exact_sums_g<3>(g, Eg, S);
+    KT = levels_to_int<3>(S.T00, Eg);
+    KX = levels_to_int<3>(S.Mx, Eg);
+    KY = levels_to_int<3>(S.My, Eg);
+    KZ = levels_to_int<3>(S.Mz, Eg);
+  }
+  const double Tu = fx::from_fixed_int(KT, 1079);
+  const double Mxu = fx::from_fixed_int(KX, 1079);
+  const double Myu = fx::from_fixed_int(KY, 1079);
+  const double Mzu = fx::from_fixed_int(KZ, 1079);
   const double MM = fma(Mxu, Mxu, fma(Myu, Myu, Mzu * Mzu));
   const double A = fma(scale_pow2(Tu, 2), Tu, -3.0 * MM);
   const double sgu = fma(2.0, Tu, sqrt_seeded(A)) * (1.0 / 3.0);
@@ -1044,9 +1076,17 @@ __device__ __forceinline__ void f32s_g_relax(float (&g)[19], const G32& s, const
 // f part: N0 (exact sum rounded to FP32 through FP64) and the flag of a non-finite f.
 __device__ __forceinline__ float f32s_f_sum(const float (&f)[19], bool& bad) {
   float N0p[3];
-  const int Ef = exact_sum_f(f, N0p);
+  const int Ef = max_exp19(f);
   bad = Ef == 255;
-  return d2f_rn_bits(scale_pow2(fx::from_fixed_int(levels_to_int(N0p, Ef), 1079), Ef - 183));
+  long long K;
+  if (min_exp19(f) >= Ef - 13) {   // two extraction levels are exact
+    exact_sum_f<2>(f, Ef, N0p);
+    K = levels_to_int<2>(N0p, Ef);
+  } else {
+    exact_sum_f<3>(f, Ef, N0p);
+    K = levels_to_int<3>(N0p, Ef);
+  }
+  return d2f_rn_bits(scale_pow2(fx::from_fixed_int(K, 1079), Ef - 183));
 }
 
 __device__ __forceinline__ void f32s_f_relax(float (&f)[19], float N0, float ux, float uy, float uz,

@@ -141,12 +141,15 @@ def test_fields_round_trip_and_host_io():
     lat.close()
 
 
-@pytest.mark.parametrize("collision, tau_q", [("mrt", 0.7), ("mrt", 0.0), ("bgk", 0.0)])
-def test_general_conversion_paths_one_step(collision, tau_q):
-    """States outside the fast path of the FP64 step: negative populations, exact
-    zeros and values 1e-12 of their node's largest (the general fixed-point
-    conversion, and outputs that take the FP64-pipe rounding).  One step against
-    the oracle, per population, relative to the largest population of the lattice."""
+@pytest.mark.parametrize("collision, tau_q, precision", [("mrt", 0.7, "fp64"), ("mrt", 0.0, "fp64"),
+                                                        ("bgk", 0.0, "fp64"), ("mrt", 0.7, "fp32")])
+def test_general_conversion_paths_one_step(collision, tau_q, precision):
+    """States outside the fast paths: negative populations, exact zeros and values
+    1e-12 of their node's largest (FP64: the general fixed-point conversion, and
+    outputs that take the FP64-pipe rounding; FP32 storage: the three-level exact
+    extraction).  One step against the oracle, per population, relative to the
+    largest population of the lattice: 1e-13 for FP64, 16 x 2^-24 for FP32 storage
+    (rounding of the stored value and of the FP32 per-link arithmetic)."""
     from paper_1211_3286_gb300.lattice import Lattice
     shape = (3, 4, 70)
     e, ux, uy, uz, n = I.periodic_box(None, seed=27, shape=shape)
@@ -169,18 +172,21 @@ def test_general_conversion_paths_one_step(collision, tau_q):
     f[6, big] = 3.0 * f[6, big]
     f, g = f.reshape(19, *shape), g.reshape(19, *shape)
     taus = dict(tau_f=0.52, tau_v=0.52, tau_e=0.55, tau_eps=0.8, tau_q=tau_q)
-    lat = Lattice(shape, collision=collision, **taus)
+    if precision == "fp32":
+        f, g = f.float().double(), g.float().double()   # the stored FP32 values
+    lat = Lattice(shape, collision=collision, precision=precision, **taus)
     lat.load_state(torch.cat([f, g]).cuda())
     lat.step(1)
     lat.check()
-    got = lat.state("cpu")
+    got = lat.state("cpu").double()
     lat.close()
     prm = O.Params(collision=collision, **taus)
     fr, gr = O.step(f, g, prm, check=False)
     assert float(gr.min()) < 0 and float(fr.min()) < 0     # the negative-output path ran
+    tol = 1e-13 if precision == "fp64" else 16 * 2.0 ** -24
     for a, b in ((got[:19], fr), (got[19:], gr)):
         err = float((a - b).abs().max() / b.abs().max())
-        assert err < 1e-13, err
+        assert err < tol, err
 
 
 def test_invalid_fields_are_rejected():
