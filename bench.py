@@ -59,13 +59,20 @@ WORKLOADS = {
                              "and recovery, same fields and taus, 200 steps"),
 }
 TAUS = dict(tau_f=0.9, tau_v=0.9, tau_e=0.55, tau_eps=0.8)
+# step counts of the workloads as configured (256^3 box: 500, 512^3 FP32 box: 200, tau sweep
+# and adjoint: 4000)
+DEFAULT_STEPS = {"box256": 500, "box128": 500, "box128_fp32": 500, "box512_fp32": 200, "tubes": 4000,
+                 "tubes_small": 200, "adjoint": 4000}
 
 # DRAM bytes (read + write) per node update of the step kernel, from ncu captures of the
 # 128^3 box with the same kernel (the 256^3 / 512^3 lattices exceed the capture size
 # rule); traffic per launch = bytes per update x nodes.  profiles/k_step_ws_box128_f64.md:
-# 1227.8 MB / 2,097,152; profiles/k_step_box128_f32.md: 588.6 MB / 2,097,152.  None
+# 1227.8 MB / 2,097,152; profiles/k_step_box128_f32.md: 587.9 MB / 2,097,152.  None
 # where the kernel changed since its capture.
-NCU_BYTES_PER_UPDATE = {"fp64": 1227.780864e6 / 2097152, "fp32": None}
+NCU_BYTES_PER_UPDATE = {"fp64": 1227.780864e6 / 2097152, "fp32": 587.880704e6 / 2097152}
+# k_tubes on the 1024-tube sweep (profiles/k_tubes_sweep1024_fp32.md): 90.03 GB over
+# 1,719,757 nodes x 200 steps
+NCU_BYTES_PER_UPDATE_TUBES = 90.03161e9 / (1719757 * 200)
 
 # FP64-pipe operations of one FP32-storage node update (the sums are exact on the
 # FP32 and integer pipes and rounded to FP64 by integer bit assembly): recovery 20
@@ -282,12 +289,13 @@ def run_tubes(args, dist, rank, ws, local):
     upd_s = nodes * args.steps / (ms / 1e3)
     gbs = 304 * upd_s / 1e9
     fp64_peak = 152 * 2 * 2.07
+    traffic = NCU_BYTES_PER_UPDATE_TUBES * nodes * args.steps if args.workload == "tubes" else None
     alu = {"bound": "alu", "achieved": FP64_OPS_PER_UPDATE_F32S * upd_s / 1e9, "peak": fp64_peak,
-           "unit": "G FP64 op/s", "traffic": None,
+           "unit": "G FP64 op/s", "traffic": traffic,
            "peak_kind": "derived: 152 SM x 2 FP64 op/clk x 2.07 GHz (measured 2.05 DFMA/clk/SM)"}
     alu["frac"] = alu["achieved"] / fp64_peak
     hbm = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
-           "traffic": None, "peak_kind": peak_kind, "note": "streaming-equivalent bytes (304 B/update); the tubes "
+           "traffic": traffic, "peak_kind": peak_kind, "note": "streaming-equivalent bytes (304 B/update); the tubes "
            "are re-read through L2"}
     roof = alu if alu["frac"] > hbm["frac"] else hbm
     if rank == 0:
@@ -484,7 +492,8 @@ def fp32_error_vs_fp64(N, steps, stream):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: the workload's own step count)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="box256", choices=sorted(WORKLOADS))
@@ -495,6 +504,8 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=20.0,
                     help="CPU budget of the oracle sample (reference arm and cpu_baseline)")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = DEFAULT_STEPS.get(args.workload, 500)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
