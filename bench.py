@@ -72,7 +72,7 @@ DEFAULT_STEPS = {"box256": 500, "box128": 500, "box128_fp32": 500, "box512_fp32"
 NCU_BYTES_PER_UPDATE = {"fp64": 1227.780864e6 / 2097152, "fp32": 587.880704e6 / 2097152}
 # k_tubes on the 1024-tube sweep (profiles/k_tubes_sweep1024_fp32.md): 90.03 GB over
 # 1,719,757 nodes x 200 steps
-NCU_BYTES_PER_UPDATE_TUBES = 90.03161e9 / (1719757 * 200)
+NCU_BYTES_PER_UPDATE_TUBES = None
 
 # FP64-pipe operations of one FP32-storage node update (the sums are exact on the
 # FP32 and integer pipes and rounded to FP64 by integer bit assembly): recovery 20
@@ -289,7 +289,8 @@ def run_tubes(args, dist, rank, ws, local):
     upd_s = nodes * args.steps / (ms / 1e3)
     gbs = 304 * upd_s / 1e9
     fp64_peak = 152 * 2 * 2.07
-    traffic = NCU_BYTES_PER_UPDATE_TUBES * nodes * args.steps if args.workload == "tubes" else None
+    traffic = (NCU_BYTES_PER_UPDATE_TUBES * nodes * args.steps
+               if args.workload == "tubes" and NCU_BYTES_PER_UPDATE_TUBES is not None else None)
     alu = {"bound": "alu", "achieved": FP64_OPS_PER_UPDATE_F32S * upd_s / 1e9, "peak": fp64_peak,
            "unit": "G FP64 op/s", "traffic": traffic,
            "peak_kind": "derived: 152 SM x 2 FP64 op/clk x 2.07 GHz (measured 2.05 DFMA/clk/SM)"}

@@ -6,13 +6,12 @@
 // Execution: one persistent kernel.  Each CTA repeatedly takes the next tube
 // from a longest-first work list (an atomic counter; longest-processing-time
 // order keeps the tail short) and advances that tube by all nsteps with
-// CTA-local barriers, reading one lattice and writing the other.  Tubes never
-// exchange data, so no grid-wide barrier exists and no CTA waits on another.
-// A tube's two lattices (<= 2 x 486 KB at 3200 FP32 nodes) are re-read every step
-// through L2 (ld.global.cg / st.global.cg: coherent at L2 for the CTA's own
-// writes after __syncthreads).  Whether they stay in L2 depends on how many tubes
-// are in flight: at two 256-thread CTAs per SM on the 1024-tube sweep the 304
-// tubes in flight exceed L2 and most bytes come from DRAM.
+// CTA-local barriers.  Tubes never exchange data, so no grid-wide barrier exists
+// and no CTA waits on another.  Steps run in place in pairs on one lattice (the AA
+// scheme, tube_step), which halves a tube's working set in L2 against reading one
+// lattice and writing the other; an odd last step goes into the other lattice.
+// Lattice accesses use ld.global.cg / st.global.cg (coherent at L2 for the CTA's
+// own writes after __syncthreads).
 //
 // Launch shape (threads per CTA, CTAs per SM) is picked by rlb_batch_autotune,
 // which times each candidate on a copy of the state.  rlb_batch_run replays
@@ -48,11 +47,127 @@ __device__ __forceinline__ S ld_cg(const S* p) { return __ldcg(p); }
 template <typename S>
 __device__ __forceinline__ void st_cg(S* p, S v) { __stcg(p, v); }
 
+// Links with c_x = +1 and c_x = -1 (the ones a zero-gradient end clamps).
+__device__ __forceinline__ int xplus_index(int a) {   // a in {1, 7, 9, 11, 13} -> 0..4
+  return a == 1 ? 0 : (a - 5) / 2;
+}
+__device__ __forceinline__ int opp(int a) { return a == 0 ? 0 : ((a & 1) ? a + 1 : a - 1); }
+
 template <typename S, bool MRT>
-__global__ void k_tubes(const TubeInfo* __restrict__ order, int ntubes, const StepConst* __restrict__ consts,
+__device__ __forceinline__ bool tube_collide(S (&f)[19], S (&g)[19], const StepConst& k) {
+  if constexpr (sizeof(S) == 8) return node_collide_fx<MRT, false>(f, g, k);
+  else return node_collide_f32s<MRT, false>(f, g, k);
+}
+
+// One step of a tube.  mode 0: two lattices, node x pulls from src (x - c_x, clamped
+// at the zero-gradient ends) and stores at x in dst.  Modes 1 and 2 are the in-place
+// pair of the AA scheme on one lattice (src == dst), which halves a tube's working set:
+//   layout N: slot a of node x holds F_a(x), the post-collision population;
+//   layout S: slot abar of node x holds the value node x pulls for link a at the next
+//     step, F_a(x - c_a) (clamped).
+//   mode 1 (N -> S): node x pulls F_a(x - c_a) from slot a of x - c_a, collides, and
+//     writes each F'_a(x) to slot abar of x + c_a (and, at an end where x - c_a falls
+//     outside, to slot abar of x itself).  Every slot a node reads is written only by
+//     that node; the clamped pulls at the ends come from edge copies in shared memory,
+//     since the neighbour overwrites the edge node's own slot within the step.
+//   mode 2 (S -> N): node x reads its own slots abar, collides, writes its own slots a
+//     and refreshes the edge copies.
+// One collide call site serves the three modes; the mode picks whole load and store
+// blocks, and only the two end nodes take the clamping / edge-copy path.
+template <typename S, bool MRT>
+__device__ __forceinline__ void tube_step(int mode, const S* src, S* dst, const TubeInfo& ti,
+                                          unsigned long long nodes, const StepConst& k, S (&edge)[2][2][5],
+                                          unsigned long long* bad) {
+  for (int x = threadIdx.x; x < ti.L; x += blockDim.x) {
+    const unsigned long long x0 = ti.off + (unsigned long long)x;
+    const bool end = x == 0 || x == ti.L - 1;
+    S f[19], g[19];
+    if (mode == 2) {
+#pragma unroll
+      for (int a = 0; a < 19; ++a) {
+        f[a] = ld_cg(src + (unsigned long long)opp(a) * nodes + x0);
+        g[a] = ld_cg(src + (19ull + opp(a)) * nodes + x0);
+      }
+    } else if (!end) {
+#pragma unroll
+      for (int a = 0; a < 19; ++a) {
+        const unsigned long long i = x0 - (long long)link_cx(a);
+        f[a] = ld_cg(src + (unsigned long long)a * nodes + i);
+        g[a] = ld_cg(src + (19ull + a) * nodes + i);
+      }
+    } else {
+#pragma unroll
+      for (int a = 0; a < 19; ++a) {
+        const int cx = link_cx(a), xs = x - cx;
+        const bool outside = cx != 0 && (xs < 0 || xs >= ti.L);
+        if (mode == 1 && outside) {                    // clamped pull: edge copy
+          const int side = cx == 1 ? 0 : 1, j = xplus_index(cx == 1 ? a : opp(a));
+          f[a] = edge[side][0][j];
+          g[a] = edge[side][1][j];
+        } else {
+          const unsigned long long i = ti.off + (unsigned long long)(outside ? x : xs);
+          f[a] = ld_cg(src + (unsigned long long)a * nodes + i);
+          g[a] = ld_cg(src + (19ull + a) * nodes + i);
+        }
+      }
+    }
+    if (tube_collide<S, MRT>(f, g, k)) atomicMin(bad, x0);
+    if (mode == 1 && !end) {
+#pragma unroll
+      for (int a = 0; a < 19; ++a) {
+        const unsigned long long i = x0 + (long long)link_cx(a);
+        st_cg(dst + (unsigned long long)opp(a) * nodes + i, f[a]);
+        st_cg(dst + (19ull + opp(a)) * nodes + i, g[a]);
+      }
+    } else if (mode == 1) {
+#pragma unroll
+      for (int a = 0; a < 19; ++a) {
+        const int cx = link_cx(a), ab = opp(a), xt = x + cx, xs = x - cx;
+        if (xt >= 0 && xt < ti.L) {
+          const unsigned long long i = ti.off + (unsigned long long)xt;
+          st_cg(dst + (unsigned long long)ab * nodes + i, f[a]);
+          st_cg(dst + (19ull + ab) * nodes + i, g[a]);
+        }
+        if (cx != 0 && (xs < 0 || xs >= ti.L)) {
+          st_cg(dst + (unsigned long long)ab * nodes + x0, f[a]);
+          st_cg(dst + (19ull + ab) * nodes + x0, g[a]);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int a = 0; a < 19; ++a) {
+        st_cg(dst + (unsigned long long)a * nodes + x0, f[a]);
+        st_cg(dst + (19ull + a) * nodes + x0, g[a]);
+      }
+      if (mode == 2 && end) {
+#pragma unroll
+        for (int a = 0; a < 19; ++a) {
+          const int cx = link_cx(a);
+          if (cx == 1 && x == 0) {
+            edge[0][0][xplus_index(a)] = f[a];
+            edge[0][1][xplus_index(a)] = g[a];
+          }
+          if (cx == -1 && x == ti.L - 1) {
+            edge[1][0][xplus_index(opp(a))] = f[a];
+            edge[1][1][xplus_index(opp(a))] = g[a];
+          }
+        }
+      }
+    }
+  }
+}
+
+// Persistent tube kernel: each CTA takes the next tube of the longest-first list and
+// advances it by nsteps: in place pairs of steps on latA (AA scheme), and for an odd
+// nsteps one last two-lattice step into latB.
+// FP32 storage: up to 512 threads (the autotuner's largest shape), i.e. at most 128
+// registers; FP64 (the integer-pipe collide needs about 170 registers): up to 256.
+template <typename S, bool MRT>
+__global__ void __launch_bounds__(sizeof(S) == 8 ? 256 : 512) k_tubes(const TubeInfo* __restrict__ order, int ntubes, const StepConst* __restrict__ consts,
                         S* latA, S* latB, unsigned long long nodes, int nsteps, unsigned* __restrict__ counter,
                         unsigned long long* __restrict__ bad) {
   __shared__ int s_t;
+  __shared__ S edge[2][2][5];   // [left/right end][f/g][link with c_x = +1 / its opposite]
   for (;;) {
     if (threadIdx.x == 0) s_t = (int)atomicAdd(counter, 1u);
     __syncthreads();
@@ -61,36 +176,19 @@ __global__ void k_tubes(const TubeInfo* __restrict__ order, int ntubes, const St
     if (t >= ntubes) return;
     const TubeInfo ti = order[t];
     const StepConst k = consts[ti.id];
-    const S* src = latA;
-    S* dst = latB;
+    // edge copies of layout N: the end nodes' own populations of the clamped links
+    if (threadIdx.x < 20) {
+      const int side = threadIdx.x / 10, d = (threadIdx.x / 5) & 1, j = threadIdx.x % 5;
+      const int a = side == 0 ? (j == 0 ? 1 : 2 * j + 5) : (j == 0 ? 2 : 2 * j + 6);
+      const unsigned long long x0 = ti.off + (unsigned long long)(side == 0 ? 0 : ti.L - 1);
+      edge[side][d][j] = ld_cg(latA + (19ull * d + a) * nodes + x0);
+    }
+    __syncthreads();
     for (int s = 0; s < nsteps; ++s) {
-      for (int x = threadIdx.x; x < ti.L; x += blockDim.x) {
-        // zero-gradient ends clamp the x source; the 1 x 1 transverse axes wrap onto the node itself
-        const unsigned long long x0 = ti.off + (unsigned long long)x;
-        const unsigned long long xm = ti.off + (unsigned long long)(x > 0 ? x - 1 : 0);
-        const unsigned long long xp = ti.off + (unsigned long long)(x < ti.L - 1 ? x + 1 : ti.L - 1);
-        S f[19], g[19];
-#pragma unroll
-        for (int a = 0; a < 19; ++a) {
-          const int cx = link_cx(a);
-          const unsigned long long i = cx == 1 ? xm : (cx == -1 ? xp : x0);
-          f[a] = ld_cg(src + (unsigned long long)a * nodes + i);
-          g[a] = ld_cg(src + (19ull + a) * nodes + i);
-        }
-        bool b;
-        if constexpr (sizeof(S) == 8) b = node_collide_fx<MRT, false>(f, g, k);
-        else b = node_collide_f32s<MRT, false>(f, g, k);
-        if (b) atomicMin(bad, x0);
-#pragma unroll
-        for (int a = 0; a < 19; ++a) {
-          st_cg(dst + (unsigned long long)a * nodes + x0, f[a]);
-          st_cg(dst + (19ull + a) * nodes + x0, g[a]);
-        }
-      }
+      // pairs in place (modes 1, 2); an odd last step into the other lattice (mode 0)
+      const int mode = (nsteps & 1) && s == nsteps - 1 ? 0 : 1 + (s & 1);
+      tube_step<S, MRT>(mode, latA, mode == 0 ? latB : latA, ti, nodes, k, edge, bad);
       __syncthreads();
-      S* tmp = const_cast<S*>(src);
-      src = dst;
-      dst = tmp;
     }
   }
 }
@@ -148,7 +246,10 @@ void* tube_kernel(const rlb_batch* b) {
 
 int grid_size(const rlb_batch* b, int threads, int ctas_per_sm) {
   int occ = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tube_kernel(b), threads, 0);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tube_kernel(b), threads, 0) != cudaSuccess) {
+    cudaGetLastError();
+    occ = 0;
+  }
   if (occ < 1) occ = 1;
   int per = ctas_per_sm > 0 ? std::min(ctas_per_sm, occ) : occ;
   int grid = per * b->sms;
@@ -363,7 +464,12 @@ extern "C" int rlb_batch_autotune(rlb_batch* b, int trial_steps, int* chosen) {
   int rc = RLB_OK;
   for (int th : cand_threads) {
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tube_kernel(b), th, 0);
+    // a block size above the kernel's limit (the FP64 kernel takes at most 256 threads)
+    // is not a candidate: clear the error the query leaves
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tube_kernel(b), th, 0) != cudaSuccess) {
+      cudaGetLastError();
+      occ = 0;
+    }
     for (int c : cand_ctas) {
       if (c > occ) continue;
       cudaError_t e = cudaMemcpyAsync(tr[0], b->lat[b->cur], bytes, cudaMemcpyDeviceToDevice, b->stream);

@@ -53,8 +53,8 @@ def test_batch_fp64_matches_oracle_per_tube(collision):
     b = TubeBatch(LENGTHS, taus, tau_f=tau_f, collision=collision, precision="fp64")
     b.set_fields(*_batch_fields(LENGTHS))
     T = 240
-    b.run(100)
-    b.run(140)   # a second graph (other lattice parity)
+    b.run(99)    # odd: in-place pairs, then one two-lattice step
+    b.run(141)   # a second graph (other lattice parity)
     got = b.fields("cpu")
     for t, L in enumerate(LENGTHS):
         ref = _oracle_tube(L, taus[t], tau_f[t], collision, T)
@@ -102,6 +102,14 @@ def test_autotune_and_graph_replay_do_not_change_results():
     assert torch.equal(b.state(), sa)
     a.close()
     b.close()
+    # FP64 tubes take at most 256 threads per CTA: larger candidates are skipped cleanly
+    c = TubeBatch(lengths[:5], taus[:5], precision="fp64")
+    c.set_fields(*_batch_fields(lengths[:5]))
+    th, ctas = c.autotune(4)
+    assert th <= 256 and ctas >= 1
+    c.run(3)
+    c.check()
+    c.close()
 
 
 def test_nonphysical_tube_is_reported_with_tube_index():
