@@ -2,13 +2,13 @@
 // checkpointed driver rlb_adjoint (include/rlb_adjoint.h).
 //
 // Per step the forward map is g^{t+1} = C(h; omega), h = S g^t, with S the pull
-// stream and C the per-node g collide of rlb_node.cuh (FP64).  The adjoint step
-// computes, per node, mu = C_h^T lambda^{t+1} and omega_bar += C_omega^T lambda^{t+1}
-// (the forward intermediates are recomputed from h, then the chain is walked
-// backwards by hand), and then lambda^t = S^T mu by a gather: the adjoint of
-// "node x pulls link a from src(x)" is "node y collects link a from every x with
-// src(x) = y" -- one node for a periodic axis, and for a zero-gradient axis also
-// the edge node's own clamped pull.
+// stream and C the per-node g collide of rlb_node.cuh (FP64).  The adjoint of step
+// t computes, per node, mu^t = C_h^T lambda^{t+1} and omega_bar += C_omega^T
+// lambda^{t+1} (the forward intermediates are recomputed from h, then the chain is
+// walked backwards by hand), where lambda^{t+1} = S^T mu^{t+1} is gathered at the node
+// inside the same kernel: the adjoint of "node x pulls link a from src(x)" is "node y
+// collects link a from every x with src(x) = y" -- one node for a periodic axis, and
+// for a zero-gradient axis also the edge node's own clamped pull.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -212,13 +212,40 @@ __device__ __forceinline__ void g_collide_vjp(const double (&h)[19], const doubl
   recovery_moments_reverse(F, sigmab, Pb, uxb, uyb, uzb, 0.0, Sab, Sdb, h0x, hb);
 }
 
-template <bool MRT>
-__global__ void __launch_bounds__(kThreads) k_adj_collide(const double* __restrict__ g, const double* __restrict__ lam,
-                                                         double* __restrict__ mu, double* __restrict__ tb, AGeo geo,
-                                                         StepConst k) {
-  const unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
-  if (i >= geo.n) return;
-  const int x = (int)(i % geo.nx), y = (int)((i / geo.nx) % geo.ny), z = (int)(i / ((unsigned long long)geo.nx * geo.ny));
+// lambda_a at node (x, y, z) from the adjoint of the pull stream: the sum of mu_a over
+// the nodes whose pull of link a lands on (x, y, z) (at most two per axis: the
+// neighbour, and at a zero-gradient end the node itself).  Loads are unrolled and
+// predicated; the order of the sum is fixed.
+__device__ __forceinline__ double gather_link(const double* __restrict__ mu_a, int x, int y, int z, int cx, int cy,
+                                              int cz, const AGeo& geo) {
+  int px[2], py[2], pz[2];
+  const int nxp = preimages(x, cx, geo.nx, geo.zgx, px);
+  const int nyp = preimages(y, cy, geo.ny, geo.zgy, py);
+  const int nzp = preimages(z, cz, geo.nz, geo.zgz, pz);
+  double acc = 0.0;
+#pragma unroll
+  for (int iz = 0; iz < 2; ++iz)
+#pragma unroll
+    for (int iy = 0; iy < 2; ++iy)
+#pragma unroll
+      for (int ix = 0; ix < 2; ++ix)
+        if (iz < nzp && iy < nyp && ix < nxp)
+          acc += mu_a[((unsigned long long)pz[iz] * geo.ny + py[iy]) * geo.nx + px[ix]];
+  return acc;
+}
+
+// One reverse step at node (x, y, z) of a (ceil(nx / blockDim), ny, nz) grid: lambda^{t+1}
+// at the node (read directly for the last step, FIRST, else gathered from the mu of the
+// step after it), then mu = C_h^T lambda^{t+1} and the omega contributions.
+template <bool MRT, bool FIRST>
+__global__ void __launch_bounds__(kThreads) k_adj_step(const double* __restrict__ g, const double* __restrict__ in,
+                                                      double* __restrict__ mu, double* __restrict__ tb, AGeo geo,
+                                                      StepConst k, int lanes) {
+  // `lanes` nodes per block along x
+  const int x = blockIdx.x * lanes + threadIdx.x;
+  if ((int)threadIdx.x >= lanes || x >= geo.nx) return;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const unsigned long long i = ((unsigned long long)z * geo.ny + y) * geo.nx + x;
   double h[19], lo[19], hb[19];
 #pragma unroll
   for (int a = 0; a < 19; ++a) {
@@ -227,7 +254,8 @@ __global__ void __launch_bounds__(kThreads) k_adj_collide(const double* __restri
     const int zs = pull_src(z, link_cz(a), geo.nz, geo.zgz);
     const unsigned long long s = ((unsigned long long)zs * geo.ny + ys) * geo.nx + xs;
     h[a] = g[(unsigned long long)a * geo.n + s];
-    lo[a] = lam[(unsigned long long)a * geo.n + i];
+    lo[a] = FIRST ? in[(unsigned long long)a * geo.n + i]
+                  : gather_link(in + (unsigned long long)a * geo.n, x, y, z, link_cx(a), link_cy(a), link_cz(a), geo);
   }
   double wvb, web, wpb;
   g_collide_vjp<MRT>(h, lo, k, hb, wvb, web, wpb);
@@ -236,26 +264,6 @@ __global__ void __launch_bounds__(kThreads) k_adj_collide(const double* __restri
   tb[i] += wvb;
   tb[geo.n + i] += web;
   tb[2 * geo.n + i] += wpb;
-}
-
-__global__ void __launch_bounds__(kThreads) k_adj_stream(const double* __restrict__ mu, double* __restrict__ lam,
-                                                        AGeo geo) {
-  const unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
-  if (i >= geo.n) return;
-  const int x = (int)(i % geo.nx), y = (int)((i / geo.nx) % geo.ny), z = (int)(i / ((unsigned long long)geo.nx * geo.ny));
-#pragma unroll
-  for (int a = 0; a < 19; ++a) {
-    int px[2], py[2], pz[2];
-    const int nxp = preimages(x, link_cx(a), geo.nx, geo.zgx, px);
-    const int nyp = preimages(y, link_cy(a), geo.ny, geo.zgy, py);
-    const int nzp = preimages(z, link_cz(a), geo.nz, geo.zgz, pz);
-    double acc = 0.0;
-    for (int iz = 0; iz < nzp; ++iz)
-      for (int iy = 0; iy < nyp; ++iy)
-        for (int ix = 0; ix < nxp; ++ix)
-          acc += mu[(unsigned long long)a * geo.n + ((unsigned long long)pz[iz] * geo.ny + py[iy]) * geo.nx + px[ix]];
-    lam[(unsigned long long)a * geo.n + i] = acc;
-  }
 }
 
 // lambda^T = dJ/dg^T and the per-node misfit.
@@ -284,16 +292,21 @@ __global__ void __launch_bounds__(kThreads) k_adj_loss(const double* __restrict_
 }
 
 // dJ/de0 of an equilibrium initial state: g^0 is linear in e0, so sum_a lambda_a g0_a / e0.
-__global__ void __launch_bounds__(kThreads) k_adj_e0(const double* __restrict__ g0, const double* __restrict__ lam,
-                                                    double* __restrict__ de0, unsigned long long n) {
-  const unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
-  if (i >= n) return;
+// dJ/de0 at node (x, y, z): lambda^0 = S^T mu^0 gathered at the node, contracted with
+// dg^eq/de of the initial state (g^eq is homogeneous of degree 1 in e at fixed u).
+__global__ void __launch_bounds__(kThreads) k_adj_e0(const double* __restrict__ g0, const double* __restrict__ mu,
+                                                    double* __restrict__ de0, AGeo geo, int lanes) {
+  const int x = blockIdx.x * lanes + threadIdx.x;
+  if ((int)threadIdx.x >= lanes || x >= geo.nx) return;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const unsigned long long i = ((unsigned long long)z * geo.ny + y) * geo.nx + x;
   double h[19];
   double acc = 0.0;
 #pragma unroll
   for (int a = 0; a < 19; ++a) {
-    h[a] = g0[(unsigned long long)a * n + i];
-    acc = fma(lam[(unsigned long long)a * n + i], h[a], acc);
+    h[a] = g0[(unsigned long long)a * geo.n + i];
+    const double l = gather_link(mu + (unsigned long long)a * geo.n, x, y, z, link_cx(a), link_cy(a), link_cz(a), geo);
+    acc = fma(l, h[a], acc);
   }
   GFwd F;
   StepConst dummy{};
@@ -326,7 +339,7 @@ int afail(rlb_handle* h, int code, const std::string& m) {
 // kept on the handle so repeated gradients replay instead of re-launching ~4 T
 // kernels one by one.
 struct AdjPlan {
-  int nsteps = -1, K = 0, nseg = 0, start_cur = 0, threads = 128;
+  int nsteps = -1, K = 0, nseg = 0, start_cur = 0, threads = 128, lanes = 128;
   double wP = 0.0, wu = 0.0;                  // misfit weights baked into the graph
   std::vector<void*> ckpt, seg, owned;
   double *lam = nullptr, *mu = nullptr, *tb = nullptr, *lossn = nullptr, *sums = nullptr, *dde0 = nullptr;
@@ -363,6 +376,9 @@ cudaError_t enqueue_adjoint(rlb_handle* h, AdjPlan* a, double wP, double wu, boo
   const size_t state_bytes = 38 * N * sizeof(double);
   const int T = a->nsteps, K = a->K, th = a->threads;
   const unsigned grid = (unsigned)((N + th - 1) / th);
+  const int lanes = a->lanes;
+  const dim3 grid3((unsigned)((h->cfg.nx + lanes - 1) / lanes), (unsigned)h->cfg.ny, (unsigned)h->cfg.nz);
+  double* mu_cur = nullptr;   // buffer holding the mu of the latest reverse step (lam / mu alternate)
   cudaStream_t st = a->cap;
   AGeo geo{h->cfg.nx, h->cfg.ny, h->cfg.nz, h->cfg.bc[0] == RLB_ZERO_GRADIENT, h->cfg.bc[1] == RLB_ZERO_GRADIENT,
            h->cfg.bc[2] == RLB_ZERO_GRADIENT, N};
@@ -399,13 +415,21 @@ cudaError_t enqueue_adjoint(rlb_handle* h, AdjPlan* a, double wP, double wu, boo
     if (e != cudaSuccess) return e;
     for (int t = t1 - 1; t >= t0; --t) {
       const double* gt = (const double*)a->seg[t - t0] + 19 * N;
-      if (mrt) k_adj_collide<true><<<grid, th, 0, st>>>(gt, a->lam, a->mu, a->tb, geo, h->k);
-      else k_adj_collide<false><<<grid, th, 0, st>>>(gt, a->lam, a->mu, a->tb, geo, h->k);
-      k_adj_stream<<<grid, th, 0, st>>>(a->mu, a->lam, geo);
+      // the last step reads lambda^T; later ones gather from the mu of the step after
+      double* out = mu_cur == a->mu ? a->lam : a->mu;
+      if (t == T - 1) {
+        out = a->mu;
+        if (mrt) k_adj_step<true, true><<<grid3, th, 0, st>>>(gt, a->lam, out, a->tb, geo, h->k, lanes);
+        else k_adj_step<false, true><<<grid3, th, 0, st>>>(gt, a->lam, out, a->tb, geo, h->k, lanes);
+      } else {
+        if (mrt) k_adj_step<true, false><<<grid3, th, 0, st>>>(gt, mu_cur, out, a->tb, geo, h->k, lanes);
+        else k_adj_step<false, false><<<grid3, th, 0, st>>>(gt, mu_cur, out, a->tb, geo, h->k, lanes);
+      }
+      mu_cur = out;
     }
   }
   ENQ(cudaGetLastError());
-  k_adj_e0<<<grid, th, 0, st>>>((const double*)a->g0copy + 19 * N, a->lam, a->dde0, N);
+  k_adj_e0<<<grid3, th, 0, st>>>((const double*)a->g0copy + 19 * N, mu_cur, a->dde0, geo, lanes);
   k_rowsum<<<3, 256, 0, st>>>(a->tb, N, a->sums);
   k_rowsum<<<1, 256, 0, st>>>(a->lossn, N, a->sums + 3);
   ENQ(cudaGetLastError());
@@ -454,6 +478,9 @@ extern "C" int rlb_adjoint(rlb_handle* h, int nsteps, int checkpoint_every, cons
     a->K = std::min(K, nsteps);
     a->nseg = (nsteps + a->K - 1) / a->K;
     a->threads = N <= 152ull * 128ull * 2ull ? 32 : 128;
+    // one node per thread (blocks with fewer active lanes, spreading a small lattice
+    // over more SMs, measured slower on GB300)
+    a->lanes = a->threads;
     a->ckpt.assign(a->nseg, nullptr);
     a->seg.assign(a->K + 1, nullptr);
     bool ok = true;
