@@ -190,13 +190,35 @@ def cpu_baseline(seconds_budget=15.0):
     f, g = O.init_populations(e, torch.stack([ux, uy, uz]), nn)
     t0 = time.perf_counter()
     steps = 0
-    while steps < 1 or (time.perf_counter() - t0 < seconds_budget and steps < 200):
+    while steps < 1 or time.perf_counter() - t0 < seconds_budget:
         f, g = O.step(f, g, prm)
         steps += 1
     dt = time.perf_counter() - t0
     return {"value": n ** 3 * steps / dt / 1e6, "unit": "MLUPS", "cores": torch.get_num_threads(),
-            "kind": "oracle", "sample": "%d^3 MRT box, %d steps, same generator and taus, FP64 oracle" % (n, steps),
+            "cpu_model": _cpu_model(), "kind": "oracle",
+            "sample": "%d^3 MRT box, %d steps, same generator and taus, FP64 oracle" % (n, steps),
             "seconds": round(dt, 2)}
+
+
+def _cpu_model():
+    """Host CPU model as lscpu or /proc/cpuinfo name it (best effort)."""
+    import platform
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.machine()
 
 
 def run_reference(args):

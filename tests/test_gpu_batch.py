@@ -79,6 +79,26 @@ def test_batch_fp32_storage_error_bound():
     b.close()
 
 
+def test_sixteen_tubes_of_the_sweep_fp64_vs_oracle():
+    """16 tubes drawn (seeded) from the 1024-tube tau sweep, run as one FP64 batch for 400
+    steps: each tube's fields against the oracle's run of that tube to 1e-12."""
+    from paper_1211_3286_gb300.batch import TubeBatch
+    lengths, taus = I.tube_sweep(1024)
+    pick = np.sort(np.random.default_rng(17).choice(len(lengths), 16, replace=False))
+    L16, t16 = lengths[pick], taus[pick]
+    b = TubeBatch(L16, t16, collision="mrt", precision="fp64")
+    b.set_fields(*_batch_fields(L16))
+    T = 400
+    b.run(T)
+    b.check()
+    got = b.fields("cpu")
+    for j in range(16):
+        ref = _oracle_tube(int(L16[j]), t16[j], t16[j][0], "mrt", T)
+        err = field_errors(_slice(got, b.offsets[j], int(L16[j])), ref)
+        assert max(err.values()) < 1e-12, (int(pick[j]), int(L16[j]), err)
+    b.close()
+
+
 def test_autotune_and_graph_replay_do_not_change_results():
     """Every node's arithmetic is independent of the launch shape: runs with the
     default shape, after autotuning, and split into several graph replays agree

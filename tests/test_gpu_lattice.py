@@ -86,6 +86,31 @@ def test_periodic_box_ragged_fp64(collision, taus):
     assert max(abs(a - float(b)) / s for a, b, s in zip(tot, tot_ref, scale)) < 1e-13
 
 
+def test_box_64_cubed_50_steps_fp64():
+    """The 3-D MRT box workload (seeded smooth fields, max|u| = 0.3, tau_v = 0.9,
+    tau_e = 0.55, tau_eps = 0.8) at 64^3 x 50 steps: every node and field against the
+    oracle to 1e-12, and the conserved totals to 1e-13."""
+    e, ux, uy, uz, n = I.periodic_box(64)
+    gpu, ref, tot, tot_ref = _run_both(e, ux, uy, uz, n, 50, "mrt", (0.9, 0.9, 0.55, 0.8, 0.0), ("periodic",) * 3)
+    err = field_errors(gpu, ref)
+    assert max(err.values()) < TOL64, err
+    scale = [float(tot_ref[0])] + [float(tot_ref[1])] * 4
+    assert max(abs(a - float(b)) / s for a, b, s in zip(tot, tot_ref, scale)) < 1e-13
+
+
+def test_box_64_cubed_fp32_storage_error_vs_fp64_oracle():
+    """FP32 population storage on the same workload at 64^3 x 200 steps: per-field error
+    against the FP64 oracle within 50 x 2^-24 x sqrt(T) (one 2^-24 rounding per stored
+    value per step, accumulated as a random walk)."""
+    e, ux, uy, uz, n = I.periodic_box(64)
+    T = 200
+    gpu, ref, _, _ = _run_both(e, ux, uy, uz, n, T, "mrt", (0.9, 0.9, 0.55, 0.8, 0.0), ("periodic",) * 3,
+                               precision="fp32")
+    err = field_errors(gpu, ref)
+    assert max(err.values()) < 50 * 2.0 ** -24 * math.sqrt(T), err
+    assert max(err.values()) > 1e-12
+
+
 def test_zero_gradient_all_axes_fp64():
     e, ux, uy, uz, n = I.periodic_box(None, seed=22, shape=(7, 6, 37))
     gpu, ref, _, _ = _run_both(e, 0.5 * ux, 0.5 * uy, 0.5 * uz, n, 30, "mrt", (0.9, 0.9, 0.55, 0.8, 0.0),
