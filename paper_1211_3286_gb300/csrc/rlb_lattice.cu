@@ -215,14 +215,16 @@ __global__ void __launch_bounds__(64 * W, RLB_WS_BLOCKS_PER_SM * 2 / W)
     Mx = dp[0] + dp[3] + dp[4] + dp[5] + dp[6];
     My = dp[1] + dp[3] - dp[4] + dp[7] + dp[8];
     Mz = dp[2] + dp[5] - dp[6] + dp[7] - dp[8];
-    const double t00 = from_fixed_dp(T00, E);
-    const double mx = from_fixed_dp(Mx, E), my = from_fixed_dp(My, E), mz = from_fixed_dp(Mz, E);
+    // in grid units (T00 < 2^62, so A/4 stays inside the range of the FP32 seeds at any
+    // scale of the populations); w is scale free
+    const double t00 = from_fixed_dp(T00, 1079);
+    const double mx = from_fixed_dp(Mx, 1079), my = from_fixed_dp(My, 1079), mz = from_fixed_dp(Mz, 1079);
     const double MM = fma(mx, mx, fma(my, my, mz * mz));
     const double A4 = fma(t00, t00, -0.75 * MM);
     const double H = t00 + sqrt_seeded(A4);
     const double iH = rcp_seeded(H);
     const double wx = mx * iH, wy = my * iH, wz = mz * iH;
-    sig = mulhi(to_fixed_abs(H, E + 7), kTwoThirds);
+    sig = mulhi(to_fixed_abs(H, 1086), kTwoThirds);
     Pf = (long long)sig - T00;
     const unsigned long long ax = to_fixed_abs(wx, 1023), ay = to_fixed_abs(wy, 1023), az = to_fixed_abs(wz, 1023);
     u.ax = ax + (ax >> 1);

@@ -229,19 +229,28 @@ __device__ __forceinline__ bool pos_finite_hi(double x) {   // x > 0, finite (hi
 }
 
 __device__ __forceinline__ void node_recover_fast(NodeMacro& m) {
-  const double MM = fma(m.Mx, m.Mx, fma(m.My, m.My, m.Mz * m.Mz));
-  const double A = fma(4.0 * m.T00, m.T00, -3.0 * MM);
+  // the recovery is homogeneous of degree 1 in (T00, M) with u scale free: run it on
+  // T00 and M divided by the power of two of T00 (exact multiplies), which keeps A
+  // inside the range of the FP32 seeds at any scale, and scale sigma and P back
+  int es = (int)(((unsigned)__double2hiint(m.T00) >> 20) & 0x7ffu) - 1023;
+  es = es < -1000 ? -1000 : (es > 1000 ? 1000 : es);
+  const double down = __hiloint2double((1023 - es) << 20, 0), up = __hiloint2double((1023 + es) << 20, 0);
+  const double T = m.T00 * down, mx = m.Mx * down, my = m.My * down, mz = m.Mz * down;
+  const double MM = fma(mx, mx, fma(my, my, mz * mz));
+  const double A = fma(4.0 * T, T, -3.0 * MM);
   const double sA = sqrt_seeded(A);
-  m.sigma = fma(2.0, m.T00, sA) * (1.0 / 3.0);
-  const double is = rcp_seeded(m.sigma);
-  m.ux = m.Mx * is;
-  m.uy = m.My * is;
-  m.uz = m.Mz * is;
-  m.P = m.sigma - m.T00;
+  const double sg = fma(2.0, T, sA) * (1.0 / 3.0);
+  const double is = rcp_seeded(sg);
+  m.ux = mx * is;
+  m.uy = my * is;
+  m.uz = mz * is;
+  const double P = sg - T;
+  m.sigma = sg * up;
+  m.P = P * up;
   m.u2 = fma(m.ux, m.ux, fma(m.uy, m.uy, m.uz * m.uz));
   // A > 0, T00 > 0, P > 0 (all finite) and u^2 < 1 (bit patterns of non-negative
   // doubles order like the values; NaN and Inf fail every test)
-  m.bad = !(pos_finite_hi(A) && pos_finite_hi(m.T00) && pos_finite_hi(m.P) &&
+  m.bad = !(pos_finite_hi(A) && pos_finite_hi(m.T00) && pos_finite_hi(P) &&
             (unsigned)__double2hiint(m.u2) < 0x3ff00000u);
 }
 
@@ -369,10 +378,10 @@ __device__ __forceinline__ bool node_collide_f64(double (&f)[19], double (&g)[19
   m.Mx = fixed_to_f64(X.Mx, Eg);
   m.My = fixed_to_f64(X.My, Eg);
   m.Mz = fixed_to_f64(X.Mz, Eg);
+  node_recover_fast(m);
   m.N0 = fixed_to_f64(exact_sum_f64(f, Ef), Ef);
   const double Sa = MRT ? fixed_to_f64(X.Sa, Eg) : 0.0;
   const double Sd = MRT ? fixed_to_f64(X.Sd, Eg) : 0.0;
-  node_recover_fast(m);
   m.bad |= (Eg == 0x7ff) || (Ef == 0x7ff);
   StepConst k = kc;
   if (ETA) {
@@ -705,16 +714,17 @@ __device__ __forceinline__ void fx_g_recover(const double (&g)[19], GState& s, U
   s.Mx = dp[0] + dp[3] + dp[4] + dp[5] + dp[6];
   s.My = dp[1] + dp[3] - dp[4] + dp[7] + dp[8];
   s.Mz = dp[2] + dp[5] - dp[6] + dp[7] - dp[8];
-  // A/4 = T00^2 - (3/4)|M|^2, H = T00 + sqrt(A/4) = 3 sigma / 2, w = M / H = 2 u / 3
-  const double t00 = from_fixed_dp(s.T00, s.Eg);
-  const double mx = from_fixed_dp(s.Mx, s.Eg), my = from_fixed_dp(s.My, s.Eg), mz = from_fixed_dp(s.Mz, s.Eg);
+  // A/4 = T00^2 - (3/4)|M|^2, H = T00 + sqrt(A/4) = 3 sigma / 2, w = M / H = 2 u / 3, in
+  // grid units (T00 < 2^62: A/4 stays inside the range of the FP32 seeds at any scale)
+  const double t00 = from_fixed_dp(s.T00, 1079);
+  const double mx = from_fixed_dp(s.Mx, 1079), my = from_fixed_dp(s.My, 1079), mz = from_fixed_dp(s.Mz, 1079);
   const double MM = fma(mx, mx, fma(my, my, mz * mz));
   const double A4 = fma(t00, t00, -0.75 * MM);
   const double H = t00 + sqrt_seeded(A4);
   const double iH = rcp_seeded(H);
   const double wx = mx * iH, wy = my * iH, wz = mz * iH;
   // sigma = 2H/3, P = sigma - T00; |u_i| 2^63 = 3/2 |w_i| 2^63
-  s.sig = mulhi(to_fixed_abs(H, s.Eg + 7), kTwoThirds);
+  s.sig = mulhi(to_fixed_abs(H, 1086), kTwoThirds);
   s.Pf = (long long)s.sig - s.T00;
   const unsigned long long ax = to_fixed_abs(wx, 1023), ay = to_fixed_abs(wy, 1023), az = to_fixed_abs(wz, 1023);
   u.ax = ax + (ax >> 1);
@@ -990,12 +1000,12 @@ __device__ __forceinline__ void f32s_g_recover(const float (&g)[19], G32& s) {
   const double Mxu = fx::from_fixed_int(KX, 1079);
   const double Myu = fx::from_fixed_int(KY, 1079);
   const double Mzu = fx::from_fixed_int(KZ, 1079);
+  const int eg = Eg - 183;
   const double MM = fma(Mxu, Mxu, fma(Myu, Myu, Mzu * Mzu));
   const double A = fma(scale_pow2(Tu, 2), Tu, -3.0 * MM);
   const double sgu = fma(2.0, Tu, sqrt_seeded(A)) * (1.0 / 3.0);
   const double is = rcp_seeded(sgu);
   const double Pu = sgu - Tu;
-  const int eg = Eg - 183;
   // per-node equilibrium constants (they cancel, sigma ~ 4P): FP64, then one rounding;
   // sigma u^2 = |M|^2 / sigma
   const double su2u = MM * is;

@@ -214,6 +214,32 @@ def test_general_conversion_paths_one_step(collision, tau_q, precision):
         assert err < tol, err
 
 
+@pytest.mark.parametrize("precision, lattice", [("fp64", "d3q19"), ("fp32", "d3q19"), ("fp64", "d2q9")])
+@pytest.mark.parametrize("scale", [2.0 ** -70, 2.0 ** 50])
+def test_power_of_two_scale_invariance(precision, lattice, scale):
+    """The g dynamics are homogeneous of degree 1 in (e, P) with u scale free: e scaled
+    by a power of two scales e and P by it exactly and leaves u and n unchanged, bit
+    for bit, after several steps (the recoveries' FP32 seeds stay in range at any scale)."""
+    from paper_1211_3286_gb300.lattice import Lattice
+    shape = (1, 6, 40) if lattice == "d2q9" else (5, 6, 40)
+    e, ux, uy, uz, n = I.periodic_box(None, seed=31, shape=shape)
+    if lattice == "d2q9":
+        uz = torch.zeros_like(uz)
+    out = []
+    for sc in (1.0, scale):
+        lat = Lattice(shape, collision="mrt", tau_v=0.9, tau_e=0.55, tau_eps=0.8, precision=precision,
+                      lattice=lattice)
+        lat.set_fields((e * sc).cuda(), ux.cuda(), uy.cuda(), uz.cuda(), n.cuda())
+        lat.step(12)
+        lat.check()
+        out.append(lat.fields("cpu"))
+        lat.close()
+    a, b = out
+    assert torch.equal(b["P"], a["P"] * scale) and torch.equal(b["e"], a["e"] * scale)
+    for k in ("ux", "uy", "uz", "n"):
+        assert torch.equal(b[k], a[k]), k
+
+
 def test_invalid_fields_are_rejected():
     from paper_1211_3286_gb300 import _lib as L
     from paper_1211_3286_gb300.lattice import Lattice
