@@ -85,7 +85,7 @@ __device__ __forceinline__ void pull19(const S* __restrict__ base, unsigned long
 #endif
 // and the FP32-storage step
 #ifndef RLB_F32_BLOCKS_PER_SM
-#define RLB_F32_BLOCKS_PER_SM 5
+#define RLB_F32_BLOCKS_PER_SM 7
 #endif
 
 template <typename S, bool MRT, bool QSEP, bool ETA = false>
