@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(kBlockX, sizeof(S) == 8 ? RLB_F64_BLOCKS_PER_S
 // registers the single-role kernel needs; out-of-range threads (x >= nx) pull a
 // clamped node, pass the barrier and store nothing.
 #ifndef RLB_WS_BLOCKS_PER_SM
-#define RLB_WS_BLOCKS_PER_SM 5
+#define RLB_WS_BLOCKS_PER_SM 7
 #endif
 // Output rounding route of the f and g warps, one bit per link pair and bit 9 for
 // the rest link: set = FP64-pipe conversion, clear = integer bit assembly with the
