@@ -160,10 +160,17 @@ __device__ __forceinline__ void tube_step(int mode, const S* src, S* dst, const 
 // Persistent tube kernel: each CTA takes the next tube of the longest-first list and
 // advances it by nsteps: in place pairs of steps on latA (AA scheme), and for an odd
 // nsteps one last two-lattice step into latB.
-// FP32 storage: up to 512 threads (the autotuner's largest shape), i.e. at most 128
-// registers; FP64 (the integer-pipe collide needs about 170 registers): up to 256.
+// FP32 storage: RLB_TUBES_F32_THREADS threads x RLB_TUBES_F32_BLOCKS CTAs per SM set the
+// register cap; FP64 (the integer-pipe collide needs about 170 registers): up to 256
+// threads.  The autotuner skips shapes the bound excludes.
+#ifndef RLB_TUBES_F32_THREADS
+#define RLB_TUBES_F32_THREADS 512
+#endif
+#ifndef RLB_TUBES_F32_BLOCKS
+#define RLB_TUBES_F32_BLOCKS 1
+#endif
 template <typename S, bool MRT>
-__global__ void __launch_bounds__(sizeof(S) == 8 ? 256 : 512) k_tubes(const TubeInfo* __restrict__ order, int ntubes, const StepConst* __restrict__ consts,
+__global__ void __launch_bounds__(sizeof(S) == 8 ? 256 : RLB_TUBES_F32_THREADS, sizeof(S) == 8 ? 1 : RLB_TUBES_F32_BLOCKS) k_tubes(const TubeInfo* __restrict__ order, int ntubes, const StepConst* __restrict__ consts,
                         S* latA, S* latB, unsigned long long nodes, int nsteps, unsigned* __restrict__ counter,
                         unsigned long long* __restrict__ bad) {
   __shared__ int s_t;
@@ -462,11 +469,15 @@ extern "C" int rlb_batch_autotune(rlb_batch* b, int trial_steps, int* chosen) {
   float best = 1e30f;
   int bt = b->threads, bc = b->ctas_per_sm;
   int rc = RLB_OK;
+  cudaFuncAttributes fa{};
+  const int max_threads =
+      cudaFuncGetAttributes(&fa, tube_kernel(b)) == cudaSuccess ? fa.maxThreadsPerBlock : 256;
+  cudaGetLastError();
   for (int th : cand_threads) {
     int occ = 0;
-    // a block size above the kernel's limit (the FP64 kernel takes at most 256 threads)
-    // is not a candidate: clear the error the query leaves
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tube_kernel(b), th, 0) != cudaSuccess) {
+    // block sizes above the kernel's launch bound are not candidates
+    if (th > max_threads ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tube_kernel(b), th, 0) != cudaSuccess) {
       cudaGetLastError();
       occ = 0;
     }
