@@ -4,10 +4,16 @@
 //
 // Data layout in HBM: two lattices (read / write, swapped every step), each
 // holding f[19][nz][ny][nx] followed by g[19][nz][ny][nx] in the storage
-// precision (FP64, or FP32 for RLB_FP32_STORAGE).  One thread owns one node:
-// it pulls the 38 populations from x - e_a (x-adjacent threads read adjacent
-// addresses, so every load is coalesced), runs the per-node collide of
-// rlb_node.cuh in registers, and writes the 38 results to its own node.
+// precision (FP64, or FP32 for RLB_FP32_STORAGE).  Populations are pulled from
+// x - e_a (x-adjacent threads read adjacent addresses, so every load is
+// coalesced), collided in registers with the per-node arithmetic of rlb_node.cuh,
+// and written to the node's own slots.
+//   FP64 (k_step_ws): two threads per node -- g warps (sums, recovery, g update)
+//     and f warps (f update) of the same nodes, u handed over in shared memory;
+//   FP32 storage, and FP64 with per-node relaxation times (k_step): one thread
+//     per node;
+//   D2Q9 (k_step_d2q9): one thread per node, with k_macro_d2q9 first when the
+//     C7 correction needs gradients of the macroscopic fields.
 #include <cuda_runtime.h>
 
 #include <climits>

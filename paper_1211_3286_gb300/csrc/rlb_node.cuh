@@ -31,6 +31,16 @@
 //     The class sums of g^eq needed for M_k.(g - g^eq) are closed forms:
 //       sum_axis g^eq = P,  sum_diag g^eq = P + 0.5 sigma u^2,
 //       q^eq_i = -(2/3) sigma u_i.
+//
+// Arithmetic variants in this file:
+//   node_collide_fx (and the warp-role kernel built from its parts): FP64
+//     populations, per-link work in 64-bit block fixed point on the integer
+//     pipes, recovery in FP64 -- the FP64 step with constant relaxation times;
+//   node_collide_f64: the same update in FP64 arithmetic -- the fixed-eta/s
+//     mode, whose relaxation times vary per node;
+//   node_collide_f32s: FP32 population storage, exact sums, FP64 recovery,
+//     FP32 per-link work;
+//   node_collide_d2q9_f64: the D2Q9 model of Sec. V.A.
 #pragma once
 #include <cmath>
 #include <cstdint>
