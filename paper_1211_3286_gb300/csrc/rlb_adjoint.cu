@@ -70,9 +70,11 @@ __device__ __forceinline__ void gforward(const double (&h)[19], const StepConst&
   F.Mz = ((F.dp[2] + F.dp[5]) - (F.dp[6] - F.dp[7])) - F.dp[8];
   F.MM = fma(F.Mx, F.Mx, fma(F.My, F.My, F.Mz * F.Mz));
   F.A = fma(4.0 * F.T00, F.T00, -3.0 * F.MM);
-  F.sA = sqrt(F.A);
+  // sqrt and reciprocal: FP32 seeds refined by Newton steps to the FP64 rounding level
+  // (a lone warp per SM issues these on its FP64 pipe, so the short forms matter)
+  F.sA = sqrt_seeded(F.A);
   F.sigma = fma(2.0, F.T00, F.sA) * (1.0 / 3.0);
-  F.is = 1.0 / F.sigma;
+  F.is = rcp_seeded(F.sigma);
   F.ux = F.Mx * F.is;
   F.uy = F.My * F.is;
   F.uz = F.Mz * F.is;
@@ -109,7 +111,7 @@ __device__ __forceinline__ void recovery_moments_reverse(const GFwd& F, double s
   T00b += (2.0 / 3.0) * sigmab;
   const double sAb = sigmab * (1.0 / 3.0);
   // sA = sqrt(A)
-  const double Ab = sAb * 0.5 / F.sA;
+  const double Ab = sAb * 0.5 * rcp_seeded(F.sA);
   // A = 4 T00^2 - 3 MM
   T00b += 8.0 * F.T00 * Ab;
   const double MMb = -3.0 * Ab;
