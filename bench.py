@@ -267,14 +267,17 @@ def run_tubes(args, dist, rank, ws, local):
     mlups = whole_job_rate(nodes * args.steps, ws, ms / 1e3)
     e2e = None
     if not args.no_e2e:
+        import ctypes
+        from paper_1211_3286_gb300 import _lib as L
         hf = [t.pin_memory() for t in fields]
         outs = [torch.empty(nodes, dtype=torch.float64).pin_memory() for _ in range(6)]
+        # one untimed host round trip (staging buffer allocated on first use)
+        b.set_fields(*hf)
+        L.rlb_batch_get_fields(b.handle, *[ctypes.c_void_p(o.data_ptr()) for o in outs], L.RLB_HOST)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         b.set_fields(*hf)
         b.run(args.steps)
-        import ctypes
-        from paper_1211_3286_gb300 import _lib as L
         L.rlb_batch_get_fields(b.handle, *[ctypes.c_void_p(o.data_ptr()) for o in outs], L.RLB_HOST)
         dt = time.perf_counter() - t0
         e2e = {"value": nodes * args.steps * ws / dt / 1e6, "unit": "MLUPS",
@@ -427,16 +430,20 @@ def run_ours(args):
     # fields, run the steps, read the final fields back
     e2e = None
     if not args.no_e2e:
+        from paper_1211_3286_gb300 import _lib as L
+        import ctypes
         hf = [t.cpu().pin_memory() for t in I.periodic_box(N, device="cuda")]
         outs = [torch.empty((N, N, N), dtype=torch.float64).pin_memory() for _ in range(6)]
+        # one untimed host round trip: the library allocates its host-I/O staging
+        # buffer on first use (one-time setup, like the warm-up steps)
+        lat.set_fields(*hf)
+        L.rlb_get_fields(lat.handle, *[ctypes.c_void_p(o.data_ptr()) for o in outs], L.RLB_HOST)
         torch.cuda.synchronize()
         if dist is not None:
             dist.barrier()
         t0 = time.perf_counter()
         lat.set_fields(*hf)
         lat.step(args.steps)
-        from paper_1211_3286_gb300 import _lib as L
-        import ctypes
         L.rlb_get_fields(lat.handle, *[ctypes.c_void_p(o.data_ptr()) for o in outs], L.RLB_HOST)
         dt = reduce_max(time.perf_counter() - t0, dist)
         e2e = {"value": whole_job_rate(nodes * args.steps, ws, dt), "unit": "MLUPS",
