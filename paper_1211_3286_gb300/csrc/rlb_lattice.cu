@@ -669,14 +669,8 @@ extern "C" int rlb_set_fields(rlb_handle* h, const double* e, const double* ux, 
   const size_t N = h->nodes;
   const double *de = e, *dx = ux, *dy = uy, *dz = uz, *dn = n;
   if (where == RLB_HOST) {
-    for (size_t i = 0; i < N; ++i) {
-      const double u2 = ux[i] * ux[i] + uy[i] * uy[i] + uz[i] * uz[i];
-      if (!(e[i] > 0) || !(n[i] > 0) || !(u2 < 1.0) || !std::isfinite(e[i]) || !std::isfinite(n[i])) {
-        char buf[128];
-        std::snprintf(buf, sizeof buf, "invalid field at node %zu (need e > 0, n > 0, |u| < 1)", i);
-        return fail(h, RLB_EINVAL, buf);
-      }
-    }
+    // host fields go to the staging buffer; k_init validates both kinds of input on
+    // the device (first bad node by atomicMin)
     int rc = ensure_stage(h);
     if (rc) return rc;
     double* s = h->d_stage;
@@ -685,7 +679,7 @@ extern "C" int rlb_set_fields(rlb_handle* h, const double* e, const double* ux, 
       RLB_CUDA(h, cudaMemcpyAsync(s + c * N, src[c], N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     de = s; dx = s + N; dy = s + 2 * N; dz = s + 3 * N; dn = s + 4 * N;
   }
-  // validate on device (RLB_DEVICE inputs) and build the equilibrium state in the spare lattice
+  // validate on the device and build the equilibrium state in the spare lattice
   const int spare = 1 - h->cur;
   const unsigned long long none = ULLONG_MAX;
   RLB_CUDA(h, cudaMemcpyAsync(h->d_bad, &none, sizeof none, cudaMemcpyHostToDevice, h->stream));
