@@ -8,7 +8,8 @@
 // walked backwards by hand), where lambda^{t+1} = S^T mu^{t+1} is gathered at the node
 // inside the same kernel: the adjoint of "node x pulls link a from src(x)" is "node y
 // collects link a from every x with src(x) = y" -- one node for a periodic axis, and
-// for a zero-gradient axis also the edge node's own clamped pull.
+// for a zero-gradient axis also the edge node's own clamped pull.  Small lattices run
+// the reverse step with four threads per node (k_adj_step_quad), larger ones with one.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -268,6 +269,214 @@ __global__ void __launch_bounds__(kThreads) k_adj_step(const double* __restrict_
   tb[2 * geo.n + i] += wpb;
 }
 
+// ---- four threads per node (small lattices)
+//
+// On a lattice of a few thousand nodes one thread per node leaves each SM with a
+// single warp whose reverse step is one long dependent chain.  k_adj_step_quad gives
+// each node four lanes of a warp: lane j takes link pairs j, j + 4 and j + 8 (the rest
+// link is read by all four), the moments and the per-pair cotangents are summed over
+// the four lanes with xor shuffles, and the short scalar chains (recovery forward and
+// backward, MRT scalars) run in all four lanes.  The arithmetic is that of
+// g_collide_vjp summed in another order.
+
+// Direction of link pair p (link 2p + 1 moves along it, link 2p + 2 against it) for a
+// pair index known only at run time, from bit masks over p: x is +1 for p in
+// {0, 3, 4, 5, 6}; y is +1 for {1, 3, 7, 8} and -1 for 4; z is +1 for {2, 5, 7} and
+// -1 for {6, 8}.
+__device__ __forceinline__ void pair_dir(int p, int& cx, int& cy, int& cz) {
+  cx = (0x079 >> p) & 1;
+  cy = ((0x19a >> p) & 1) * (p == 4 ? -1 : 1);
+  cz = ((0x1e4 >> p) & 1) * ((p == 6 || p == 8) ? -1 : 1);
+}
+
+// c * v for c in {-1, 0, 1}, without a multiply
+__device__ __forceinline__ double sel(int c, double v) { return c == 0 ? 0.0 : (c > 0 ? v : -v); }
+
+// sum over the four lanes of one node (lanes 4m .. 4m + 3), returned to all four
+__device__ __forceinline__ double quad_sum(double v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  return v;
+}
+
+// One reverse step on a (ceil(4 nx / blockDim), ny, nz) grid, blockDim a multiple of 32.
+template <bool MRT, bool FIRST>
+__global__ void __launch_bounds__(kThreads) k_adj_step_quad(const double* __restrict__ g,
+                                                           const double* __restrict__ in, double* __restrict__ mu,
+                                                           double* __restrict__ tb, AGeo geo, StepConst k) {
+  const int j = threadIdx.x & 3;
+  const int xg = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 2);
+  const bool valid = xg < geo.nx;
+  const int x = valid ? xg : geo.nx - 1;   // lanes past the row repeat its last node and store nothing
+  const int y = blockIdx.y, z = blockIdx.z;
+  const unsigned long long n = geo.n;
+  const unsigned long long i = ((unsigned long long)z * geo.ny + y) * geo.nx + x;
+  const double h0 = g[i];
+  const double l0 = in[i];   // the rest link's lambda is mu at the node itself
+  double ha[3], hb[3], la[3], lb[3];
+  int cd[3][3];
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    const int p = j + 4 * s;
+    int cx = 0, cy = 0, cz = 0;
+    if (p <= 8) pair_dir(p, cx, cy, cz);
+    cd[s][0] = cx;
+    cd[s][1] = cy;
+    cd[s][2] = cz;
+    ha[s] = hb[s] = la[s] = lb[s] = 0.0;
+    if (p <= 8) {
+      const unsigned long long a1 = 2 * p + 1, a2 = 2 * p + 2;
+      const unsigned long long s1 = ((unsigned long long)pull_src(z, cz, geo.nz, geo.zgz) * geo.ny +
+                                     pull_src(y, cy, geo.ny, geo.zgy)) * geo.nx + pull_src(x, cx, geo.nx, geo.zgx);
+      const unsigned long long s2 = ((unsigned long long)pull_src(z, -cz, geo.nz, geo.zgz) * geo.ny +
+                                     pull_src(y, -cy, geo.ny, geo.zgy)) * geo.nx + pull_src(x, -cx, geo.nx, geo.zgx);
+      ha[s] = g[a1 * n + s1];
+      hb[s] = g[a2 * n + s2];
+      la[s] = FIRST ? in[a1 * n + i] : gather_link(in + a1 * n, x, y, z, cx, cy, cz, geo);
+      lb[s] = FIRST ? in[a2 * n + i] : gather_link(in + a2 * n, x, y, z, -cx, -cy, -cz, geo);
+    }
+  }
+  // ---- forward intermediates: moments over the four lanes, then the scalar chain
+  double Sa = 0, Sd = 0, Mx = 0, My = 0, Mz = 0;
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    const int p = j + 4 * s;
+    const double sp = ha[s] + hb[s], dp = ha[s] - hb[s];
+    if (p < 3) Sa += sp;
+    else Sd += sp;   // zero for p > 8
+    Mx += sel(cd[s][0], dp);
+    My += sel(cd[s][1], dp);
+    Mz += sel(cd[s][2], dp);
+  }
+  Sa = quad_sum(Sa);
+  Sd = quad_sum(Sd);
+  Mx = quad_sum(Mx);
+  My = quad_sum(My);
+  Mz = quad_sum(Mz);
+  const double T00 = (h0 + Sa) + Sd;
+  const double MM = fma(Mx, Mx, fma(My, My, Mz * Mz));
+  const double A = fma(4.0 * T00, T00, -3.0 * MM);
+  const double sA = sqrt_seeded(A);
+  const double sigma = fma(2.0, T00, sA) * (1.0 / 3.0);
+  const double is = rcp_seeded(sigma);
+  const double ux = Mx * is, uy = My * is, uz = Mz * is;
+  const double P = sigma - T00;
+  const double u2 = fma(ux, ux, fma(uy, uy, uz * uz));
+  const double su2 = sigma * u2, P3 = 3.0 * P;
+  const double kg = fma(-1.5, su2, P3), geq0 = fma(-0.5, su2, sigma - P3);
+  double ne = 0, np = 0;
+  if (MRT) {
+    const double n0 = h0 - geq0, nA = Sa - P, nD = fma(-0.5, su2, Sd - P);
+    ne = fma(8.0, nD, fma(-11.0, nA, -30.0 * n0));
+    np = fma(-4.0, nA, fma(12.0, n0, nD));
+  }
+  // ---- reverse, per pair, then summed over the four lanes
+  const double om = k.omv, om1 = k.omv1;
+  const double wA = 1.0 / 18.0, wD = 1.0 / 36.0;
+  const double SA2 = 2.0 * k.gA_s * sigma, SD2 = 2.0 * k.gD_s * sigma, AA = k.gA_a * sigma, AD = k.gD_a * sigma;
+  double SAb = 0, SDb = 0, AAb = 0, ADb = 0, KAb = 0, KDb = 0, wvb = 0, uxb = 0, uyb = 0, uzb = 0;
+  double o1[3], o2[3];
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    const int p = j + 4 * s;
+    const double c = (sel(cd[s][0], ux) + sel(cd[s][1], uy)) + sel(cd[s][2], uz);
+    o1[s] = om1 * la[s];
+    o2[s] = om1 * lb[s];
+    wvb -= ha[s] * la[s] + hb[s] * lb[s];
+    const double evb = la[s] + lb[s], odb = la[s] - lb[s];
+    double cub;
+    if (p < 3) {
+      SAb += evb * c * c; KAb += evb; AAb += odb * c;
+      cub = evb * SA2 * c + odb * AA;
+    } else {   // all zero for p > 8
+      SDb += evb * c * c; KDb += evb; ADb += odb * c;
+      cub = evb * SD2 * c + odb * AD;
+    }
+    uxb += sel(cd[s][0], cub);
+    uyb += sel(cd[s][1], cub);
+    uzb += sel(cd[s][2], cub);
+  }
+  SAb = quad_sum(SAb);
+  SDb = quad_sum(SDb);
+  AAb = quad_sum(AAb);
+  ADb = quad_sum(ADb);
+  KAb = quad_sum(KAb);
+  KDb = quad_sum(KDb);
+  wvb = quad_sum(wvb);
+  uxb = quad_sum(uxb);
+  uyb = quad_sum(uyb);
+  uzb = quad_sum(uzb);
+  // rest link: out0 = (1 - om) h0 + om geq0 (+ 30 ae - 12 ap)
+  const double o0 = om1 * l0;
+  wvb += (geq0 - h0) * l0;
+  double geq0b = om * l0;
+  double aeb = 30.0 * l0, apb = -12.0 * l0;
+  aeb += 11.0 * KAb - 8.0 * KDb;
+  apb += 4.0 * KAb - KDb;
+  const double kgb = om * (wA * KAb + wD * KDb);
+  wvb += kg * (wA * KAb + wD * KDb);
+  const double sw = 4.5 * (wA * SAb + wD * SDb) + 3.0 * (wA * AAb + wD * ADb);
+  double sigmab = om * sw;
+  wvb += sigma * sw;
+  double Sab = 0, Sdb = 0, Pb = 0, su2b = 0, h0x = 0, web = 0, wpb = 0;
+  if (MRT) {
+    const double neb = k.ce * aeb, npb = k.cp * apb;
+    const double ceb = ne * aeb * (1.0 / 2394.0), cpb = np * apb * (1.0 / 252.0);
+    web = ceb;
+    wpb = cpb;
+    wvb -= ceb + cpb;
+    const double n0b = -30.0 * neb + 12.0 * npb;
+    const double nAb = -11.0 * neb - 4.0 * npb;
+    const double nDb = 8.0 * neb + npb;
+    h0x = n0b;
+    geq0b -= n0b;
+    Sab = nAb;
+    Sdb = nDb;
+    Pb = -nAb - nDb;
+    su2b = -0.5 * nDb;
+  }
+  // geq0 = sigma - P3 - 0.5 su2 ; kg = P3 - 1.5 su2 ; P3 = 3 P ; su2 = sigma u2
+  sigmab += geq0b;
+  su2b += -0.5 * geq0b - 1.5 * kgb;
+  Pb += 3.0 * (kgb - geq0b);
+  sigmab += u2 * su2b;
+  const double u2b = sigma * su2b;
+  uxb += 2.0 * ux * u2b;
+  uyb += 2.0 * uy * u2b;
+  uzb += 2.0 * uz * u2b;
+  // P = sigma - T00 ; u = M / sigma ; sigma = (2 T00 + sqrt(A)) / 3 ; A = 4 T00^2 - 3 |M|^2
+  sigmab += Pb;
+  double T00b = -Pb;
+  double Mxb = is * uxb, Myb = is * uyb, Mzb = is * uzb;
+  sigmab -= is * is * (Mx * uxb + My * uyb + Mz * uzb);
+  T00b += (2.0 / 3.0) * sigmab;
+  const double Ab = sigmab * (1.0 / 6.0) * rcp_seeded(sA);
+  T00b += 8.0 * T00 * Ab;
+  const double MMb = -6.0 * Ab;
+  Mxb += Mx * MMb;
+  Myb += My * MMb;
+  Mzb += Mz * MMb;
+  // T00 = h0 + Sa + Sd
+  Sab += T00b;
+  Sdb += T00b;
+  if (!valid) return;
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    const int p = j + 4 * s;
+    if (p > 8) continue;
+    const double spb = p < 3 ? Sab : Sdb;
+    const double dpb = (sel(cd[s][0], Mxb) + sel(cd[s][1], Myb)) + sel(cd[s][2], Mzb);
+    mu[(unsigned long long)(2 * p + 1) * n + i] = o1[s] + (spb + dpb);
+    mu[(unsigned long long)(2 * p + 2) * n + i] = o2[s] + (spb - dpb);
+  }
+  if (j == 0) {
+    mu[i] = o0 + (T00b + h0x);
+    tb[i] += wvb;
+    tb[n + i] += web;
+    tb[2 * n + i] += wpb;
+  }
+}
+
 // lambda^T = dJ/dg^T and the per-node misfit.
 __global__ void __launch_bounds__(kThreads) k_adj_loss(const double* __restrict__ g, const double* __restrict__ tP,
                                                       const double* __restrict__ tux, const double* __restrict__ tuy,
@@ -342,6 +551,7 @@ int afail(rlb_handle* h, int code, const std::string& m) {
 // kernels one by one.
 struct AdjPlan {
   int nsteps = -1, K = 0, nseg = 0, start_cur = 0, threads = 128, lanes = 128;
+  bool quad = false;                          // reverse steps with four threads per node
   double wP = 0.0, wu = 0.0;                  // misfit weights baked into the graph
   std::vector<void*> ckpt, seg, owned;
   double *lam = nullptr, *mu = nullptr, *tb = nullptr, *lossn = nullptr, *sums = nullptr, *dde0 = nullptr;
@@ -380,6 +590,7 @@ cudaError_t enqueue_adjoint(rlb_handle* h, AdjPlan* a, double wP, double wu, boo
   const unsigned grid = (unsigned)((N + th - 1) / th);
   const int lanes = a->lanes;
   const dim3 grid3((unsigned)((h->cfg.nx + lanes - 1) / lanes), (unsigned)h->cfg.ny, (unsigned)h->cfg.nz);
+  const dim3 grid4((unsigned)((4ull * h->cfg.nx + th - 1) / th), (unsigned)h->cfg.ny, (unsigned)h->cfg.nz);
   double* mu_cur = nullptr;   // buffer holding the mu of the latest reverse step (lam / mu alternate)
   cudaStream_t st = a->cap;
   AGeo geo{h->cfg.nx, h->cfg.ny, h->cfg.nz, h->cfg.bc[0] == RLB_ZERO_GRADIENT, h->cfg.bc[1] == RLB_ZERO_GRADIENT,
@@ -421,8 +632,16 @@ cudaError_t enqueue_adjoint(rlb_handle* h, AdjPlan* a, double wP, double wu, boo
       double* out = mu_cur == a->mu ? a->lam : a->mu;
       if (t == T - 1) {
         out = a->mu;
-        if (mrt) k_adj_step<true, true><<<grid3, th, 0, st>>>(gt, a->lam, out, a->tb, geo, h->k, lanes);
-        else k_adj_step<false, true><<<grid3, th, 0, st>>>(gt, a->lam, out, a->tb, geo, h->k, lanes);
+        if (a->quad) {
+          if (mrt) k_adj_step_quad<true, true><<<grid4, th, 0, st>>>(gt, a->lam, out, a->tb, geo, h->k);
+          else k_adj_step_quad<false, true><<<grid4, th, 0, st>>>(gt, a->lam, out, a->tb, geo, h->k);
+        } else {
+          if (mrt) k_adj_step<true, true><<<grid3, th, 0, st>>>(gt, a->lam, out, a->tb, geo, h->k, lanes);
+          else k_adj_step<false, true><<<grid3, th, 0, st>>>(gt, a->lam, out, a->tb, geo, h->k, lanes);
+        }
+      } else if (a->quad) {
+        if (mrt) k_adj_step_quad<true, false><<<grid4, th, 0, st>>>(gt, mu_cur, out, a->tb, geo, h->k);
+        else k_adj_step_quad<false, false><<<grid4, th, 0, st>>>(gt, mu_cur, out, a->tb, geo, h->k);
       } else {
         if (mrt) k_adj_step<true, false><<<grid3, th, 0, st>>>(gt, mu_cur, out, a->tb, geo, h->k, lanes);
         else k_adj_step<false, false><<<grid3, th, 0, st>>>(gt, mu_cur, out, a->tb, geo, h->k, lanes);
@@ -483,6 +702,11 @@ extern "C" int rlb_adjoint(rlb_handle* h, int nsteps, int checkpoint_every, cons
     // one node per thread (blocks with fewer active lanes, spreading a small lattice
     // over more SMs, measured slower on GB300)
     a->lanes = a->threads;
+    // below ~2 warps per SM the one-thread-per-node step is one thread's dependent
+    // chain; four threads per node shorten it (the scalar chain is repeated, so on
+    // larger lattices, where the FP64 pipe is the limit, one thread per node is kept).
+    // 1600-node tube, 4000 steps: 109 -> 87 ms per gradient on GB300.
+    a->quad = a->threads == 32;
     a->ckpt.assign(a->nseg, nullptr);
     a->seg.assign(a->K + 1, nullptr);
     bool ok = true;
