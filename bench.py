@@ -69,7 +69,7 @@ DEFAULT_STEPS = {"box256": 500, "box128": 500, "box128_fp32": 500, "box512_fp32"
 # rule); traffic per launch = bytes per update x nodes.  profiles/k_step_ws_box128_f64.md:
 # 1245.1 MB / 2,097,152; profiles/k_step_box128_f32.md: 587.7 MB / 2,097,152.  None
 # where the kernel changed since its capture.
-NCU_BYTES_PER_UPDATE = {"fp64": 1245.11744e6 / 2097152, "fp32": 587.74784e6 / 2097152}
+NCU_BYTES_PER_UPDATE = {"fp64": None, "fp32": 587.74784e6 / 2097152}
 # k_tubes on the 1024-tube sweep (profiles/k_tubes_sweep1024_fp32.md): 52.04 GB over
 # 1,719,757 nodes x 200 steps
 NCU_BYTES_PER_UPDATE_TUBES = 52.044659e9 / (1719757 * 200)
@@ -80,11 +80,10 @@ NCU_BYTES_PER_UPDATE_TUBES = 52.044659e9 / (1719757 * 200)
 # equilibrium constants 4.
 FP64_OPS_PER_UPDATE_F32S = 25
 
-# FP64-pipe operations (FMA = 1, int64 -> FP64 conversion = 1) of one FP64 node
-# update: recovery 18 (|M|^2 3, A/4 2, sqrt 6, H 1, reciprocal 3, u 3), 4 roundings of
-# the exact sums T00, M and 38 roundings of the relaxed links; the sums, equilibria
-# and relaxation run in 64-bit fixed point on the integer pipes.
-FP64_OPS_PER_UPDATE = 60
+# FP64-pipe operations (int64 -> FP64 conversion = 1) of one FP64 node update: the 38
+# roundings of the relaxed links.  The sums, the recovery, the equilibria and the
+# relaxation run in 64-bit fixed point on the integer pipes.
+FP64_OPS_PER_UPDATE = 38
 
 
 def _dist():

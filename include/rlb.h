@@ -56,9 +56,10 @@ extern "C" {
 #define RLB_MRT                  1   /* Eqs. 30-35 (D3Q19 moment basis) for g */
 #define RLB_PERIODIC             0
 #define RLB_ZERO_GRADIENT        1   /* "open" end: a pull from outside takes the edge node */
-#define RLB_FP64                 0   /* populations stored in FP64; the recovery runs in FP64 and the per-link
-                                        update in 64-bit block fixed point (every value on the grid of its
-                                        node's largest: 2^-56 of it), rounded once to FP64 per link */
+#define RLB_FP64                 0   /* populations stored in FP64; the step runs in 64-bit block fixed point
+                                        (every value on the grid of its node's largest: 2^-56 of it; the
+                                        recovery's root and reciprocal to ~2^-58), rounded once to FP64 per
+                                        link; the output fields are recovered in FP64 */
 #define RLB_FP32_STORAGE         1   /* populations stored in FP32; sums, recovery, gamma in FP64 */
 #define RLB_CORR_NONE            0
 #define RLB_CORR_C7              1   /* Eq. 37 with C_7 of Eq. 38 added to the m_7 = p_xx moment */

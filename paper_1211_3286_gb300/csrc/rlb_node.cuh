@@ -483,8 +483,10 @@ __device__ __forceinline__ bool node_collide_f64(double (&f)[19], double (&g)[19
 // keeps its bits down to 2^-56 of the node's largest population.  Sums (Eq. 10),
 // equilibria (Eqs. 7-9), the BGK relaxation (Eqs. 5-6) and the MRT projection
 // (Eq. 35) are integer adds and 64 x 64 -> high-64 products, each off by at most a
-// few grid units; only the recovery (Eq. 10 inverted) runs in FP64.  Each output
-// is rounded once to FP64.
+// few grid units.  The recovery (Eq. 10 inverted) runs on the same integers: its
+// square root and reciprocal are FP32 seeds refined by fixed-point Newton steps, to
+// about 2^-58 (FP64 rounding is 2^-53).  Each output is rounded once to FP64, the
+// only FP64-pipe work (38 conversions per node).
 //
 // Output rounding to FP64 has two routes: integer bit assembly (ALU pipe; the FP64
 // pipe only for negative or tiny values) or __ll2double_rn (FP64 pipe).  RLB_FX_OUT_F / RLB_FX_OUT_G pick the route for the
@@ -519,6 +521,29 @@ __device__ __forceinline__ long long mulhi_su(long long y, unsigned long long b,
 __device__ __forceinline__ long long with_sign(unsigned long long v, unsigned s) {
   const unsigned long long m = 0ull - (unsigned long long)s;
   return (long long)((v ^ m) - m);
+}
+
+// a 2^-64 as a float (significand truncated to 24 bits) for a nonzero a, by moving bits
+__device__ __forceinline__ float top_float(unsigned long long a) {
+  const unsigned lz = (unsigned)__clzll((long long)a);
+  const unsigned m = (unsigned)((a << lz) >> 40);
+  return __uint_as_float(((126u - lz) << 23) | (m & 0x7fffffu));
+}
+// x 2^S as an integer for a positive normal float x with x 2^S < 2^64 (S >= 22)
+template <int S>
+__device__ __forceinline__ unsigned long long fixed_from_float(float x) {
+  const unsigned b = __float_as_uint(x);
+  return (unsigned long long)((b & 0x7fffffu) | 0x800000u) << ((b >> 23) - (150u - S));
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
 }
 
 // |x| * 2^(Er - 1086), truncated, for a double x whose biased exponent is at most Er:
@@ -694,7 +719,7 @@ __device__ __forceinline__ void ufix_products(UFix& u) {
 
 // g half of the integer-pipe FP64 collide: block exponent, fixed-point values, the
 // conserved sums (Eq. 10, exact on the grid), the recovery (Eq. 10 inverted under
-// P = e/3) in FP64 on the once-rounded sums, and u on the fixed grid.
+// P = e/3) on those exact sums, and u on the fixed grid.
 struct GState {
   long long G[19];
   long long dp[3];            // pair differences of the axis pairs (energy-flux rows)
@@ -724,30 +749,53 @@ __device__ __forceinline__ void fx_g_recover(const double (&g)[19], GState& s, U
   s.Mx = dp[0] + dp[3] + dp[4] + dp[5] + dp[6];
   s.My = dp[1] + dp[3] - dp[4] + dp[7] + dp[8];
   s.Mz = dp[2] + dp[5] - dp[6] + dp[7] - dp[8];
-  // A/4 = T00^2 - (3/4)|M|^2, H = T00 + sqrt(A/4) = 3 sigma / 2, w = M / H = 2 u / 3, in
-  // grid units (T00 < 2^62: A/4 stays inside the range of the FP32 seeds at any scale)
-  const double t00 = from_fixed_dp(s.T00, 1079);
-  const double mx = from_fixed_dp(s.Mx, 1079), my = from_fixed_dp(s.My, 1079), mz = from_fixed_dp(s.Mz, 1079);
-  const double MM = fma(mx, mx, fma(my, my, mz * mz));
-  const double A4 = fma(t00, t00, -0.75 * MM);
-  const double H = t00 + sqrt_seeded(A4);
-  const double iH = rcp_seeded(H);
-  const double wx = mx * iH, wy = my * iH, wz = mz * iH;
-  // sigma = 2H/3, P = sigma - T00; |u_i| 2^63 = 3/2 |w_i| 2^63
-  s.sig = mulhi(to_fixed_abs(H, 1086), kTwoThirds);
+  // Recovery (Eq. 10 inverted under P = e/3) in 64-bit fixed point, without an FP64
+  // instruction: with A/4 = T00^2 - (3/4)|M|^2 and H = T00 + sqrt(A/4) = 3 sigma / 2,
+  // sigma = 2H/3 and u = 3M / (2H).  T00 is shifted left until its top bit is set and M
+  // with it (|M_i| < T00 in every physical state), so the square root and the
+  // reciprocal act on numbers in a fixed binary range: an FP32 seed each, then two
+  // Newton steps on 64-bit products (sigma within a few grid units, u within 2^-58).
+  const unsigned long long amx = (unsigned long long)(s.Mx < 0 ? -s.Mx : s.Mx);
+  const unsigned long long amy = (unsigned long long)(s.My < 0 ? -s.My : s.My);
+  const unsigned long long amz = (unsigned long long)(s.Mz < 0 ? -s.Mz : s.Mz);
+  const unsigned long long T = s.T00 > 0 ? (unsigned long long)s.T00 : 1ull;
+  bool badr = (s.T00 <= 0) | (amx >= T) | (amy >= T) | (amz >= T);
+  const int nsh = __clzll((long long)T);                       // >= 2: T00 < 2^62
+  const unsigned long long Tn = T << nsh;
+  const unsigned long long mxn = badr ? 0ull : amx << nsh, myn = badr ? 0ull : amy << nsh,
+                           mzn = badr ? 0ull : amz << nsh;
+  const unsigned long long t2 = mulhi(Tn, Tn);
+  const unsigned long long m2q = (mulhi(mxn, mxn) >> 2) + (mulhi(myn, myn) >> 2) + (mulhi(mzn, mzn) >> 2);
+  badr |= m2q >= (t2 >> 2);                                    // |M| >= T00: |u| >= 1
+  const unsigned long long a = t2 - 3ull * (badr ? 0ull : m2q);  // (A/4) 2^(2 nsh - 64), in (2^60, 2^64)
+  // rho = (a 2^-64)^(-1/2) in (1, 4) as Y = rho 2^61 (< 2^63 even for a seed of 4):
+  // Y <- Y (3 - a Y^2) / 2
+  unsigned long long Y = fixed_from_float<61>(rsqrt_approx(top_float(a)));
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const unsigned long long q = mulhi(a, mulhi(Y, Y));          // a rho^2 2^58
+    Y = mulhi(Y, (3ull << 62) - (q << 4)) << 1;
+  }
+  const unsigned long long Sq = mulhi(a, Y) << 3;              // sqrt(A/4) 2^nsh, in (2^62, 2^64)
+  const unsigned long long h = (Tn >> 1) + (Sq >> 1);          // H 2^(nsh - 1), in (1.5 2^62, 2^64)
+  // R = 2^126 / h: R <- R (2 - h R 2^-126)
+  unsigned long long R = fixed_from_float<62>(rcp_approx(top_float(h)));
+#pragma unroll
+  for (int it = 0; it < 2; ++it) R = mulhi(R, (1ull << 63) - mulhi(h, R)) << 2;
+  // sigma = 2H/3 = (4/3) h 2^(1 - nsh); |u_i| 2^63 = (3/4)(|M_i| 2^nsh / h) 2^63 = (3/2) mulhi(|M_i| 2^nsh, R)
+  s.sig = mulhi(h, kTwoThirds) >> (nsh - 1);
   s.Pf = (long long)s.sig - s.T00;
-  const unsigned long long ax = to_fixed_abs(wx, 1023), ay = to_fixed_abs(wy, 1023), az = to_fixed_abs(wz, 1023);
-  u.ax = ax + (ax >> 1);
-  u.ay = ay + (ay >> 1);
-  u.az = az + (az >> 1);
-  u.sx = (unsigned)__double2hiint(wx) >> 31;
-  u.sy = (unsigned)__double2hiint(wy) >> 31;
-  u.sz = (unsigned)__double2hiint(wz) >> 31;
+  const unsigned long long ux = mulhi(mxn, R), uy = mulhi(myn, R), uz = mulhi(mzn, R);
+  u.ax = ux + (ux >> 1);
+  u.ay = uy + (uy >> 1);
+  u.az = uz + (uz >> 1);
+  u.sx = (unsigned)((unsigned long long)s.Mx >> 63);
+  u.sy = (unsigned)((unsigned long long)s.My >> 63);
+  u.sz = (unsigned)((unsigned long long)s.Mz >> 63);
   ufix_products(u);
-  // non-physical: A < 0 (or not finite), T00 <= 0, P <= 0, u^2 >= 1, or a block
-  // exponent outside the normal range the grid needs
-  s.bad = (s.Eg < 64) | (s.Eg > 2046) | ((unsigned)__double2hiint(A4) >= 0x7ff00000u) | (s.T00 <= 0) |
-          (s.Pf <= 0) | (u.xx + u.yy + u.zz >= (1ull << 62));
+  // non-physical: T00 <= 0, |M| >= T00 (A < 0 among them), P <= 0, u^2 >= 1, or a
+  // block exponent outside the normal range the grid needs
+  s.bad = (s.Eg < 64) | (s.Eg > 2046) | badr | (s.Pf <= 0) | (u.xx + u.yy + u.zz >= (1ull << 62));
 }
 
 // g relaxation: Eq. 6 (BGK) or Eq. 35 (MRT as BGK plus the e, eps, q projections)
