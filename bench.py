@@ -33,11 +33,11 @@ sys.path.insert(0, ROOT)
 import torch  # noqa: E402
 
 WORKLOADS = {
-    "box256": dict(N=256, precision="fp64", dtype="f64 (FP64 storage and recovery; links in 64-bit block fixed point)",
+    "box256": dict(N=256, precision="fp64", dtype="f64 (FP64 storage; sums, recovery and links in 64-bit block fixed point)",
                    bytes_per_update=608,
                    desc="3-D MRT periodic box, D3Q19, 256^3 nodes, FP64, tau_v=0.9 tau_e=0.55 tau_eps=0.8, "
                         "seeded smooth fields (max|u|=0.3), 500 steps"),
-    "box128": dict(N=128, precision="fp64", dtype="f64 (FP64 storage and recovery; links in 64-bit block fixed point)",
+    "box128": dict(N=128, precision="fp64", dtype="f64 (FP64 storage; sums, recovery and links in 64-bit block fixed point)",
                    bytes_per_update=608,
                    desc="3-D MRT periodic box, D3Q19, 128^3 nodes, FP64 (small profiling case of the 256^3 "
                         "workload, 1.3 GB of lattices)"),

@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(64 * W, RLB_WS_BLOCKS_PER_SM * 2 / W)
   unsigned long long sig = 0;
   bool b = (E < 64) | (E > 2046);
   if (is_g) {
-    // conserved sums (Eq. 10) and the recovery in FP64 on the once-rounded sums
+    // conserved sums (Eq. 10) and the recovery on them, in fixed point
     long long sp[9], dp[9];
 #pragma unroll
     for (int p = 0; p < 9; ++p) {
@@ -221,30 +221,15 @@ __global__ void __launch_bounds__(64 * W, RLB_WS_BLOCKS_PER_SM * 2 / W)
     Mx = dp[0] + dp[3] + dp[4] + dp[5] + dp[6];
     My = dp[1] + dp[3] - dp[4] + dp[7] + dp[8];
     Mz = dp[2] + dp[5] - dp[6] + dp[7] - dp[8];
-    // in grid units (T00 < 2^62, so A/4 stays inside the range of the FP32 seeds at any
-    // scale of the populations); w is scale free
-    const double t00 = from_fixed_dp(T00, 1079);
-    const double mx = from_fixed_dp(Mx, 1079), my = from_fixed_dp(My, 1079), mz = from_fixed_dp(Mz, 1079);
-    const double MM = fma(mx, mx, fma(my, my, mz * mz));
-    const double A4 = fma(t00, t00, -0.75 * MM);
-    const double H = t00 + sqrt_seeded(A4);
-    const double iH = rcp_seeded(H);
-    const double wx = mx * iH, wy = my * iH, wz = mz * iH;
-    sig = mulhi(to_fixed_abs(H, 1086), kTwoThirds);
+    bool br;
+    sig = fx_recover(T00, Mx, My, Mz, u, br);
     Pf = (long long)sig - T00;
-    const unsigned long long ax = to_fixed_abs(wx, 1023), ay = to_fixed_abs(wy, 1023), az = to_fixed_abs(wz, 1023);
-    u.ax = ax + (ax >> 1);
-    u.ay = ay + (ay >> 1);
-    u.az = az + (az >> 1);
-    u.sx = (unsigned)__double2hiint(wx) >> 31;
-    u.sy = (unsigned)__double2hiint(wy) >> 31;
-    u.sz = (unsigned)__double2hiint(wz) >> 31;
     s_ax[slot] = u.ax;
     s_ay[slot] = u.ay;
     s_az[slot] = u.az;
     s_sg[slot] = u.sx | (u.sy << 1) | (u.sz << 2);
     ufix_products(u);
-    b |= ((unsigned)__double2hiint(A4) >= 0x7ff00000u) | (T00 <= 0) | (Pf <= 0) | (u.xx + u.yy + u.zz >= (1ull << 62));
+    b |= br | (Pf <= 0) | (u.xx + u.yy + u.zz >= (1ull << 62));
   } else {
     N0 = X[0];
 #pragma unroll

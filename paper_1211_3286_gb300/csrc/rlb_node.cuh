@@ -717,6 +717,57 @@ __device__ __forceinline__ void ufix_products(UFix& u) {
   u.yz = mulhi(u.ay, u.az);
 }
 
+// Recovery (Eq. 10 inverted under P = e/3) in 64-bit fixed point from the exact sums
+// T00 and M on a node's grid, without an FP64 instruction: with A/4 = T00^2 - (3/4)|M|^2
+// and H = T00 + sqrt(A/4) = 3 sigma / 2, sigma = 2H/3 and u = 3M / (2H).  T00 is shifted
+// left until its top bit is set and M with it (|M_i| < T00 in every physical state), so
+// the square root and the reciprocal act on numbers in a fixed binary range: an FP32
+// seed each, then two Newton steps on 64-bit products (sigma within a few grid units,
+// u within 2^-58).  Returns sigma on the grid and |u_i| 2^63 with sign bits in u; sets
+// bad for T00 <= 0 or |M| >= T00 (|u| >= 1).
+__device__ __forceinline__ unsigned long long fx_recover(long long T00, long long Mx, long long My, long long Mz,
+                                                         UFix& u, bool& bad) {
+  using namespace fx;
+  const unsigned long long amx = (unsigned long long)(Mx < 0 ? -Mx : Mx);
+  const unsigned long long amy = (unsigned long long)(My < 0 ? -My : My);
+  const unsigned long long amz = (unsigned long long)(Mz < 0 ? -Mz : Mz);
+  const unsigned long long T = T00 > 0 ? (unsigned long long)T00 : 1ull;
+  bool badr = (T00 <= 0) | (amx >= T) | (amy >= T) | (amz >= T);
+  const int nsh = __clzll((long long)T);                       // >= 2: T00 < 2^62
+  const unsigned long long Tn = T << nsh;
+  const unsigned long long mxn = badr ? 0ull : amx << nsh, myn = badr ? 0ull : amy << nsh,
+                           mzn = badr ? 0ull : amz << nsh;
+  const unsigned long long t2 = mulhi(Tn, Tn);
+  const unsigned long long m2q = (mulhi(mxn, mxn) >> 2) + (mulhi(myn, myn) >> 2) + (mulhi(mzn, mzn) >> 2);
+  badr |= m2q >= (t2 >> 2);                                    // |M| >= T00: |u| >= 1
+  const unsigned long long a = t2 - 3ull * (badr ? 0ull : m2q);  // (A/4) 2^(2 nsh - 64), in (2^60, 2^64)
+  // rho = (a 2^-64)^(-1/2) in (1, 4) as Y = rho 2^61 (< 2^63 even for a seed of 4):
+  // Y <- Y (3 - a Y^2) / 2
+  unsigned long long Y = fixed_from_float<61>(rsqrt_approx(top_float(a)));
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const unsigned long long q = mulhi(a, mulhi(Y, Y));          // a rho^2 2^58
+    Y = mulhi(Y, (3ull << 62) - (q << 4)) << 1;
+  }
+  const unsigned long long Sq = mulhi(a, Y) << 3;              // sqrt(A/4) 2^nsh, in (2^62, 2^64)
+  const unsigned long long h = (Tn >> 1) + (Sq >> 1);          // H 2^(nsh - 1), in (1.5 2^62, 2^64)
+  // R = 2^126 / h: R <- R (2 - h R 2^-126)
+  unsigned long long R = fixed_from_float<62>(rcp_approx(top_float(h)));
+#pragma unroll
+  for (int it = 0; it < 2; ++it) R = mulhi(R, (1ull << 63) - mulhi(h, R)) << 2;
+  // |u_i| 2^63 = (3/4)(|M_i| 2^nsh / h) 2^63 = (3/2) mulhi(|M_i| 2^nsh, R)
+  const unsigned long long ux = mulhi(mxn, R), uy = mulhi(myn, R), uz = mulhi(mzn, R);
+  u.ax = ux + (ux >> 1);
+  u.ay = uy + (uy >> 1);
+  u.az = uz + (uz >> 1);
+  u.sx = (unsigned)((unsigned long long)Mx >> 63);
+  u.sy = (unsigned)((unsigned long long)My >> 63);
+  u.sz = (unsigned)((unsigned long long)Mz >> 63);
+  bad = badr;
+  // sigma = 2H/3 = (4/3) h 2^(1 - nsh)
+  return mulhi(h, kTwoThirds) >> (nsh - 1);
+}
+
 // g half of the integer-pipe FP64 collide: block exponent, fixed-point values, the
 // conserved sums (Eq. 10, exact on the grid), the recovery (Eq. 10 inverted under
 // P = e/3) on those exact sums, and u on the fixed grid.
@@ -749,49 +800,9 @@ __device__ __forceinline__ void fx_g_recover(const double (&g)[19], GState& s, U
   s.Mx = dp[0] + dp[3] + dp[4] + dp[5] + dp[6];
   s.My = dp[1] + dp[3] - dp[4] + dp[7] + dp[8];
   s.Mz = dp[2] + dp[5] - dp[6] + dp[7] - dp[8];
-  // Recovery (Eq. 10 inverted under P = e/3) in 64-bit fixed point, without an FP64
-  // instruction: with A/4 = T00^2 - (3/4)|M|^2 and H = T00 + sqrt(A/4) = 3 sigma / 2,
-  // sigma = 2H/3 and u = 3M / (2H).  T00 is shifted left until its top bit is set and M
-  // with it (|M_i| < T00 in every physical state), so the square root and the
-  // reciprocal act on numbers in a fixed binary range: an FP32 seed each, then two
-  // Newton steps on 64-bit products (sigma within a few grid units, u within 2^-58).
-  const unsigned long long amx = (unsigned long long)(s.Mx < 0 ? -s.Mx : s.Mx);
-  const unsigned long long amy = (unsigned long long)(s.My < 0 ? -s.My : s.My);
-  const unsigned long long amz = (unsigned long long)(s.Mz < 0 ? -s.Mz : s.Mz);
-  const unsigned long long T = s.T00 > 0 ? (unsigned long long)s.T00 : 1ull;
-  bool badr = (s.T00 <= 0) | (amx >= T) | (amy >= T) | (amz >= T);
-  const int nsh = __clzll((long long)T);                       // >= 2: T00 < 2^62
-  const unsigned long long Tn = T << nsh;
-  const unsigned long long mxn = badr ? 0ull : amx << nsh, myn = badr ? 0ull : amy << nsh,
-                           mzn = badr ? 0ull : amz << nsh;
-  const unsigned long long t2 = mulhi(Tn, Tn);
-  const unsigned long long m2q = (mulhi(mxn, mxn) >> 2) + (mulhi(myn, myn) >> 2) + (mulhi(mzn, mzn) >> 2);
-  badr |= m2q >= (t2 >> 2);                                    // |M| >= T00: |u| >= 1
-  const unsigned long long a = t2 - 3ull * (badr ? 0ull : m2q);  // (A/4) 2^(2 nsh - 64), in (2^60, 2^64)
-  // rho = (a 2^-64)^(-1/2) in (1, 4) as Y = rho 2^61 (< 2^63 even for a seed of 4):
-  // Y <- Y (3 - a Y^2) / 2
-  unsigned long long Y = fixed_from_float<61>(rsqrt_approx(top_float(a)));
-#pragma unroll
-  for (int it = 0; it < 2; ++it) {
-    const unsigned long long q = mulhi(a, mulhi(Y, Y));          // a rho^2 2^58
-    Y = mulhi(Y, (3ull << 62) - (q << 4)) << 1;
-  }
-  const unsigned long long Sq = mulhi(a, Y) << 3;              // sqrt(A/4) 2^nsh, in (2^62, 2^64)
-  const unsigned long long h = (Tn >> 1) + (Sq >> 1);          // H 2^(nsh - 1), in (1.5 2^62, 2^64)
-  // R = 2^126 / h: R <- R (2 - h R 2^-126)
-  unsigned long long R = fixed_from_float<62>(rcp_approx(top_float(h)));
-#pragma unroll
-  for (int it = 0; it < 2; ++it) R = mulhi(R, (1ull << 63) - mulhi(h, R)) << 2;
-  // sigma = 2H/3 = (4/3) h 2^(1 - nsh); |u_i| 2^63 = (3/4)(|M_i| 2^nsh / h) 2^63 = (3/2) mulhi(|M_i| 2^nsh, R)
-  s.sig = mulhi(h, kTwoThirds) >> (nsh - 1);
+  bool badr;
+  s.sig = fx_recover(s.T00, s.Mx, s.My, s.Mz, u, badr);
   s.Pf = (long long)s.sig - s.T00;
-  const unsigned long long ux = mulhi(mxn, R), uy = mulhi(myn, R), uz = mulhi(mzn, R);
-  u.ax = ux + (ux >> 1);
-  u.ay = uy + (uy >> 1);
-  u.az = uz + (uz >> 1);
-  u.sx = (unsigned)((unsigned long long)s.Mx >> 63);
-  u.sy = (unsigned)((unsigned long long)s.My >> 63);
-  u.sz = (unsigned)((unsigned long long)s.Mz >> 63);
   ufix_products(u);
   // non-physical: T00 <= 0, |M| >= T00 (A < 0 among them), P <= 0, u^2 >= 1, or a
   // block exponent outside the normal range the grid needs
