@@ -129,12 +129,15 @@ __global__ void __launch_bounds__(kBlockX, sizeof(S) == 8 ? RLB_F64_BLOCKS_PER_S
 // FP64 step with warp roles (the integer-pipe collide of rlb_node.cuh).  A block of
 // 2 W warps serves 32 W nodes along x: warps [0, W) pull and relax g, warps [W, 2W)
 // pull and relax f of the same nodes.  The g warps recover u (Eq. 10 inverted) and
-// hand it to the f warps through shared memory across one block barrier.  Each
+// hand it to the f warps through shared memory across one barrier per warp pair.  Each
 // thread holds one distribution of one node, so twice as many warps fit in the
 // registers the single-role kernel needs; out-of-range threads (x >= nx) pull a
 // clamped node, pass the barrier and store nothing.
-#ifndef RLB_WS_BLOCKS_PER_SM
-#define RLB_WS_BLOCKS_PER_SM 7
+// Resident warps per SM the launch bounds ask of the large-lattice blocks (the
+// register cap follows: 32 warps -> 64 registers, a few spilled); small lattices
+// keep 14 64-thread blocks (72 registers).
+#ifndef RLB_WS_WARPS_PER_SM
+#define RLB_WS_WARPS_PER_SM 32
 #endif
 // Output rounding route of the f and g warps, one bit per link pair and bit 9 for
 // the rest link: set = FP64-pipe conversion, clear = integer bit assembly with the
@@ -145,13 +148,14 @@ __global__ void __launch_bounds__(kBlockX, sizeof(S) == 8 ? RLB_F64_BLOCKS_PER_S
 #ifndef RLB_WS_OUT_G
 #define RLB_WS_OUT_G 0x3ff
 #endif
-// warps per role in the blocks of large lattices
+// warps per role in the blocks of large lattices (4: 256-thread blocks serving 128
+// nodes along x)
 #ifndef RLB_WS_WARPS
-#define RLB_WS_WARPS 2
+#define RLB_WS_WARPS 4
 #endif
 
 template <int W, bool MRT, bool QSEP>
-__global__ void __launch_bounds__(64 * W, RLB_WS_BLOCKS_PER_SM * 2 / W)
+__global__ void __launch_bounds__(64 * W, W == 1 ? 14 : RLB_WS_WARPS_PER_SM / (2 * W))
     k_step_ws(const double* __restrict__ src, double* __restrict__ dst, Geo geo, StepConst k,
               unsigned long long* __restrict__ bad) {
   __shared__ unsigned long long s_ax[32 * W], s_ay[32 * W], s_az[32 * W];
@@ -235,7 +239,9 @@ __global__ void __launch_bounds__(64 * W, RLB_WS_BLOCKS_PER_SM * 2 / W)
 #pragma unroll
     for (int a = 1; a < 19; ++a) N0 += X[a];
   }
-  __syncthreads();
+  // g warp i hands u to f warp i only: one named barrier per warp pair (ids 1..W, 64
+  // threads each), so a slow g warp holds back its own f warp, not the whole block
+  asm volatile("bar.sync %0, 64;" ::"r"(1 + (is_g ? warp : warp - W)) : "memory");
   if (!is_g) {
     u.ax = s_ax[slot];
     u.ay = s_ay[slot];

@@ -586,8 +586,8 @@ __device__ __forceinline__ long long to_fixed_pos(double x, int Er) {
 // The same through the FP64 pipe's int64 conversion (round to nearest even).
 __device__ __forceinline__ double from_fixed_dp(long long K, int E) {
   const double d = __ll2double_rn(K);
-  const int hi = __double2hiint(d);
-  return __hiloint2double(K ? hi + (int)((unsigned)(E - 1079) << 20) : hi, __double2loint(d));
+  const int hi = __double2hiint(d);   // 0 exactly when K = 0 (then the low word is 0 too)
+  return __hiloint2double(hi ? hi + (int)((unsigned)(E - 1079) << 20) : 0, __double2loint(d));
 }
 // K * 2^(E - 1079) rounded to the nearest double (ties to even) by integer bit
 // assembly for 2^32 <= K < 2^63, the range of a population near its node's largest;
