@@ -68,8 +68,22 @@ __device__ __forceinline__ int src_plus(int i, int n, int zg) {   // source of a
   return i < n - 1 ? i + 1 : (zg ? n - 1 : 0);
 }
 
+// Read-only population load.  FP64 populations are streamed past L1 (each value is
+// read once per step from its plane; L2 serves the neighbouring rows' reuse), which
+// leaves L1 to the FP64 step's register spills.
+#ifndef RLB_LD_NOALLOC
+#define RLB_LD_NOALLOC 1
+#endif
 template <typename S>
 __device__ __forceinline__ S ldg_nc(const S* p) { return __ldg(p); }
+#if RLB_LD_NOALLOC
+template <>
+__device__ __forceinline__ double ldg_nc<double>(const double* p) {
+  double v;
+  asm("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
+#endif
 
 // Gather the 19 populations of one distribution arriving at node (x, y, z):
 // link a comes from (x - cx, y - cy, z - cz).
