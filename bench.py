@@ -66,10 +66,11 @@ DEFAULT_STEPS = {"box256": 500, "box128": 500, "box128_fp32": 500, "box512_fp32"
 
 # DRAM bytes (read + write) per node update of the step kernel, from ncu captures of the
 # 128^3 box with the same kernel (the 256^3 / 512^3 lattices exceed the capture size
-# rule); traffic per launch = bytes per update x nodes.  profiles/k_step_ws_box128_f64.md:
-# 1282.3 MB / 2,097,152; profiles/k_step_box128_f32.md: 587.7 MB / 2,097,152.  None
-# where the kernel changed since its capture.
-NCU_BYTES_PER_UPDATE = {"fp64": 1282.316032e6 / 2097152, "fp32": 587.74784e6 / 2097152}
+# rule); traffic per launch = bytes per update x nodes.  profiles/k_step_box128_f32.md:
+# 587.7 MB / 2,097,152.  None where the kernel changed since its capture (the FP64 step:
+# profiles/k_step_ws_box128_f64.md measured 1282.3 MB / 2,097,152 before its loads
+# took the L1::no_allocate hint).
+NCU_BYTES_PER_UPDATE = {"fp64": None, "fp32": 587.74784e6 / 2097152}
 # k_tubes on the 1024-tube sweep (profiles/k_tubes_sweep1024_fp32.md): 52.04 GB over
 # 1,719,757 nodes x 200 steps
 NCU_BYTES_PER_UPDATE_TUBES = 52.044659e9 / (1719757 * 200)
