@@ -86,6 +86,19 @@ def test_periodic_box_ragged_fp64(collision, taus):
     assert max(abs(a - float(b)) / s for a, b, s in zip(tot, tot_ref, scale)) < 1e-13
 
 
+def test_ragged_box_wide_blocks_fp64():
+    """A lattice above the small-lattice threshold (more than 38,912 nodes), so the FP64
+    step runs its 256-thread blocks of 128 nodes along x, with nx = 150: the second
+    block's first g and f warps hold 22 valid lanes and its other warps none.  Every
+    lane passes its warp pair's barrier and only valid lanes store.  Zero-gradient x
+    ends put the clamped pulls at the ragged tail."""
+    e, ux, uy, uz, n = I.periodic_box(None, seed=28, shape=(17, 16, 150))
+    bc = ("zero_gradient", "periodic", "periodic")
+    gpu, ref, tot, tot_ref = _run_both(e, ux, uy, uz, n, 15, "mrt", (0.9, 0.9, 0.55, 0.8, 0.0), bc)
+    err = field_errors(gpu, ref)
+    assert max(err.values()) < TOL64, err
+
+
 def test_box_64_cubed_50_steps_fp64():
     """The 3-D MRT box workload (seeded smooth fields, max|u| = 0.3, tau_v = 0.9,
     tau_e = 0.55, tau_eps = 0.8) at 64^3 x 50 steps: every node and field against the
