@@ -41,6 +41,13 @@ Readings of the paper taken here (the paper is silent or D2Q9-only on these):
   * The initial state is f = f^eq, g = g^eq of the initial fields.  The state after
     step t is the post-collision lattice; the fields reported at t are Eq. 10 plus
     the recovery applied to that stored lattice.
+  * The C_7 correction (Eqs. 37-38) is written for a flow along the paper's z.  It
+    is the amount by which the first-order flux of m^eq_7 exceeds the relativistic
+    Navier-Stokes one, so its sign follows the flow axis's place in the D2Q9 row
+    m_7 = c_x^2 - c_y^2: C_7 = E_x - E_y, with E_a the Eq. 38 bracket along axis a
+    (the printed sign for a flow along x, the opposite for a flow along y).  The
+    theta term takes the coefficient 1 of Eq. A17 (the printed Eq. 38 has 2;
+    ``Params.c7_theta`` selects either).  Derivatives are central differences.
 """
 from __future__ import annotations
 
@@ -349,7 +356,8 @@ class Params:
     tau_q: float = 0.0                  # <= 0 means tau_q = tau_v
     bc: tuple = (PERIODIC, PERIODIC, PERIODIC)
     lattice: str = "d3q19"               # or "d2q9" (the MRT model of Sec. V.A)
-    correction: bool = False             # D2Q9 MRT only: the C_7 term of Eqs. 37-38 (flow along x)
+    correction: bool = False             # D2Q9 MRT only: the C_7 term of Eqs. 37-38 (flow along x or y)
+    c7_theta: float = 1.0                # coefficient of Eq. 38's theta term: 1 (Eq. A17), 2 (as printed)
     eta_over_s: float = 0.0              # > 0: tau_g (BGK) or tau_v (MRT) per node from eta/s (Sec. II,
                                          # III.B); tau_f <= 0 then means tau_f = tau_g; for MRT tau_e,
                                          # tau_eps, tau_q are read as the ratios (tau_x - 1/2)/(tau_v - 1/2)
@@ -388,7 +396,7 @@ def collide(f, g, prm: Params, check: bool = True):
     elif prm.collision == "mrt":
         S = relaxation_diag(prm.tau_v, prm.tau_e, prm.tau_eps, prm.tq(), lat=prm.lattice)
         if prm.correction:
-            gs = collide_mrt_corrected(g, geq, S, fl, prm.bc[0])
+            gs = collide_mrt_corrected(g, geq, S, fl, prm.bc, prm.c7_theta)
         else:
             gs = collide_mrt(g, geq, S)
     else:
@@ -396,29 +404,64 @@ def collide(f, g, prm: Params, check: bool = True):
     return fs, gs
 
 
-def _ddx(q, bc_x):
-    """Central difference along x (the tube axis, last dimension), delta_x = 1; a
-    zero-gradient end uses the edge value for the missing neighbour, a periodic axis
-    wraps."""
-    if bc_x == PERIODIC:
-        qp, qm = torch.roll(q, -1, dims=-1), torch.roll(q, 1, dims=-1)
+def _dd(q, axis, bc):
+    """Central difference along a lattice axis (axis 0 = x, the last tensor
+    dimension; axis 1 = y, the one before it), delta_x = 1.  A zero-gradient end
+    uses the edge value for the missing neighbour, a periodic axis wraps."""
+    dim = q.dim() - 1 - axis
+    if bc == PERIODIC:
+        qp, qm = torch.roll(q, -1, dims=dim), torch.roll(q, 1, dims=dim)
     else:
-        qp = torch.cat([q[..., 1:], q[..., -1:]], dim=-1)
-        qm = torch.cat([q[..., :1], q[..., :-1]], dim=-1)
+        n = q.shape[dim]
+        qp = torch.cat([q.narrow(dim, 1, n - 1), q.narrow(dim, n - 1, 1)], dim=dim)
+        qm = torch.cat([q.narrow(dim, 0, 1), q.narrow(dim, 0, n - 1)], dim=dim)
     return 0.5 * (qp - qm)
 
 
-def correction_c7(fl: Fields, bc_x):
-    """Eq. 38 with the flow along x (the paper's z):
-    C_7 = 2 dt [u dx(c_s^2 sigma - P) - c_s^2 sigma gamma^-1 u dx(gamma) - u dx(sigma u^2)
-               + u^2 theta dx(sigma u)],   theta = 1 + 1 / ((e/P + 1) gamma^2 - 1)."""
-    sg, P, gam, u = fl.sigma, fl.P, fl.gamma, fl.u[0]
+C7_WEIGHTS = (2.0, 2.0, 2.0)   # Eq. 38's factor 2 on its first three terms (the fourth: theta_coef)
+
+
+def c7_axis_terms(fl: Fields, axis, d):
+    """The four terms of Eq. 38 for a flow along one lattice axis a (the paper's z),
+    with derivative operator d = d/dx_a:
+      t1 = u_a d(c_s^2 sigma - P)                 (the change of Eq. 28)
+      t2 = -c_s^2 sigma gamma^-1 u_a d(gamma)     (gamma d(u_a) -> d(gamma u_a))
+      t3 = -u_a d(sigma u_a^2)                    (third order, from d_t1(sigma u_a^2))
+      t4 = u_a^2 theta d(sigma u_a),  theta = 1 + 1 / ((e/P + 1) gamma^2 - 1)."""
+    sg, P, gam, u = fl.sigma, fl.P, fl.gamma, fl.u[axis]
     theta = 1.0 + 1.0 / ((fl.e / P + 1.0) * gam * gam - 1.0)
-    return 2.0 * (u * _ddx(CS2 * sg - P, bc_x) - CS2 * sg / gam * u * _ddx(gam, bc_x)
-                  - u * _ddx(sg * u * u, bc_x) + u * u * theta * _ddx(sg * u, bc_x))
+    return (u * d(CS2 * sg - P), -CS2 * sg / gam * u * d(gam), -u * d(sg * u * u), u * u * theta * d(sg * u))
 
 
-def collide_mrt_corrected(g, geq, S, fl: Fields, bc_x):
+def c7_axis_term(fl: Fields, axis, d, theta_coef=1.0):
+    """E_a = 2 (t1 + t2 + t3) + theta_coef t4 (terms of ``c7_axis_terms``): the part
+    of the first-order flux of the moment sum (c_a^2 - c_t^2) g (t the transverse
+    axis) that the relativistic Navier-Stokes stress 2 eta d_a(gamma u_a) does not
+    contain (Eq. A14 with Eqs. A9, A12, A17, A19).  Eq. A17 gives t4 the coefficient
+    1 (theta_coef = 1); the printed Eq. 38 carries it inside the factor 2
+    (theta_coef = 2)."""
+    w = tuple(C7_WEIGHTS) + (theta_coef,)
+    t = c7_axis_terms(fl, axis, d)
+    return w[0] * t[0] + w[1] * t[1] + w[2] * t[2] + w[3] * t[3]
+
+
+def correction_c7(fl: Fields, bc, theta_coef=1.0, deriv=None):
+    """C_7 of Eq. 38 for the D2Q9 moment m_7 = sum (c_x^2 - c_y^2) g (Eq. 34,
+    m^eq_7 = sigma (u_x^2 - u_y^2)), for a flow along either lattice axis:
+      C_7 = E_x - E_y   (c7_axis_term along x and along y).
+    Eq. 37 makes C the amount by which the first-order flux of m^eq is corrected, so
+    C_7 carries the sign of the flow axis inside m_7: + for a flow along x (the
+    first axis of p_xx), - for a flow along y.  For the paper's one-dimensional
+    problems one of the two terms vanishes.  ``bc`` gives (bc_x, bc_y, ...);
+    derivatives are the scheme's central differences (``_dd``) unless ``deriv(q,
+    axis)`` is given."""
+    if deriv is None:
+        deriv = lambda q, a: _dd(q, a, bc[a])   # noqa: E731
+    return (c7_axis_term(fl, 0, lambda q: deriv(q, 0), theta_coef)
+            - c7_axis_term(fl, 1, lambda q: deriv(q, 1), theta_coef))
+
+
+def collide_mrt_corrected(g, geq, S, fl: Fields, bc, theta_coef=1.0):
     """Eq. 37: m* = m - S (m - m^eq) + (I - S/2) C with C_7 of Eq. 38 the only nonzero
     entry; m_7 is the D2Q9 moment with m^eq_7 = sigma (u_x^2 - u_y^2) (row 'pxx')."""
     Q = g.shape[0]
@@ -432,7 +475,7 @@ def collide_mrt_corrected(g, geq, S, fl: Fields, bc_x):
     Sd = S.to(g.dtype)
     mstar = m - Sd.reshape(Q, 1) * (m - meq)
     k7 = MRT_ROWS_D2Q9.index("pxx")
-    mstar[k7] = mstar[k7] + (1.0 - Sd[k7] / 2.0) * correction_c7(fl, bc_x).reshape(-1)
+    mstar[k7] = mstar[k7] + (1.0 - Sd[k7] / 2.0) * correction_c7(fl, bc, theta_coef).reshape(-1)
     return (Minv @ mstar).reshape(shape)
 
 
