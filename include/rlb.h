@@ -46,7 +46,8 @@ extern "C" {
 #define RLB_ENOMEM    2  /* device or host allocation failed */
 #define RLB_ECUDA     3  /* a CUDA runtime call failed */
 #define RLB_ENONPHYS  4  /* the device flagged a non-physical node during stepping */
-#define RLB_ETIMEOUT  5  /* a bounded device-side wait gave up */
+#define RLB_ETIMEOUT  5  /* reserved for a bounded device-side wait that gives up; no kernel of this
+                             library waits on another CTA or device, so no call returns it */
 
 /* lattice, equation of state, collision, boundary, precision, memory space */
 #define RLB_D3Q19               19
@@ -62,7 +63,9 @@ extern "C" {
                                         link; the output fields are recovered in FP64 */
 #define RLB_FP32_STORAGE         1   /* populations stored in FP32; sums, recovery, gamma in FP64 */
 #define RLB_CORR_NONE            0
-#define RLB_CORR_C7              1   /* Eq. 37 with C_7 of Eq. 38 added to the m_7 = p_xx moment */
+#define RLB_CORR_C7              1   /* Eq. 37 with C_7 of Eq. 38 on the m_7 = p_xx moment; its theta term
+                                        with the coefficient 1 of Eq. A17 */
+#define RLB_CORR_C7_PRINTED      2   /* the same with Eq. 38's theta term as printed (coefficient 2) */
 #define RLB_HOST                 0
 #define RLB_DEVICE               1
 
@@ -79,13 +82,20 @@ extern "C" {
  *   stream   a cudaStream_t (NULL = legacy default stream) on which all work of
  *            this handle is enqueued.
  *   correction  RLB_CORR_C7 adds the error-correction term of Eqs. 37-38 to the
- *            D2Q9 MRT collision: m* = m - S (m - m^eq) + (1 - s_7/2) C_7 e_7 with
- *            C_7 = 2 [u dx(c_s^2 sigma - P) - c_s^2 sigma u dx(gamma)/gamma
- *                     - u dx(sigma u^2) + u^2 theta dx(sigma u)],
- *            theta = 1 + 1/((e/P + 1) gamma^2 - 1), the flow along x (the paper's z),
- *            central differences of the fields pulled at the neighbours (a
- *            zero-gradient end reuses the edge value).  Each step then runs two
- *            kernels (fields, then the corrected collide).
+ *            D2Q9 MRT collision: m* = m - S (m - m^eq) + (1 - s_7/2) C_7 e_7 on the
+ *            moment m_7 = sum (c_x^2 - c_y^2) g (m^eq_7 = sigma (u_x^2 - u_y^2), Eq. 34),
+ *            with C_7 = E_x - E_y and, for each axis a,
+ *            E_a = 2 [u_a da(c_s^2 sigma - P) - c_s^2 sigma u_a da(gamma)/gamma
+ *                     - u_a da(sigma u_a^2)] + k u_a^2 theta da(sigma u_a),
+ *            theta = 1 + 1/((e/P + 1) gamma^2 - 1).  E_a is Eq. 38 for a flow along
+ *            axis a (the paper's z); its sign in C_7 follows that axis's place in
+ *            m_7, so a tube along x (the printed sign) and a tube along y (the paper's
+ *            4 x 800 geometry, the opposite sign) are the same problem relabelled.
+ *            k = 1 (RLB_CORR_C7, the coefficient Eq. A17 gives) or 2
+ *            (RLB_CORR_C7_PRINTED, Eq. 38 as printed).  Derivatives are central
+ *            differences of the fields pulled at the neighbours (a zero-gradient end
+ *            reuses the edge value).  Each step then runs two kernels (fields, then
+ *            the corrected collide).
  *   eta_over_s  > 0 selects the paper's fixed-eta/s relaxation (Sec. II and III.B):
  *            per node and step, tau_g = 1/2 + eta / (c_s^2 (e + P) gamma) with
  *            eta = (eta/s) s, s = 4 n - n ln(n / n_eq), n_eq = 16 T^3 / pi^2 and
@@ -104,7 +114,7 @@ typedef struct rlb_config {
   int bc[3];        /* per axis x, y, z: RLB_PERIODIC | RLB_ZERO_GRADIENT */
   int precision;    /* RLB_FP64 | RLB_FP32_STORAGE */
   void* stream;
-  int correction;   /* RLB_CORR_NONE | RLB_CORR_C7 (RLB_D2Q9 + RLB_MRT only, flow along x) */
+  int correction;   /* RLB_CORR_NONE | RLB_CORR_C7 | RLB_CORR_C7_PRINTED (RLB_D2Q9 + RLB_MRT only) */
   double eta_over_s; /* > 0: per-node tau_g / tau_v from eta/s (RLB_FP64); 0: constant taus */
 } rlb_config;
 
@@ -182,8 +192,11 @@ long long rlb_steps_done(const rlb_handle* h);
  * the order differs from rlb_conserved_totals, so the two agree to round-off)
  * but takes the state itself rather than a handle and calls no cudaMalloc,
  * cudaFree or other allocating routine.
- *   state      device pointer to a raw state in the rlb_save_state layout
+ *   state      device pointer to a raw D3Q19 state in the rlb_save_state layout
  *              (f[19][nodes] then g[19][nodes]), FP64 or FP32 per `precision`.
+ *              D3Q19 states only: a D2Q9 state (f[9] g[9], from an RLB_D2Q9
+ *              handle) holds 18 values per node, and passing one makes the call
+ *              read past the end of the caller's buffer.
  *   nodes      lattice nodes, 1 <= nodes <= RLB_NOALLOC_MAX_NODES; larger sizes
  *              return RLB_EINVAL with the limit in rlb_last_error(NULL).
  *   precision  RLB_FP64 or RLB_FP32_STORAGE.

@@ -20,7 +20,7 @@ RLB_BGK, RLB_MRT = 0, 1
 RLB_PERIODIC, RLB_ZERO_GRADIENT = 0, 1
 RLB_FP64, RLB_FP32_STORAGE = 0, 1
 RLB_HOST, RLB_DEVICE = 0, 1
-RLB_CORR_NONE, RLB_CORR_C7 = 0, 1
+RLB_CORR_NONE, RLB_CORR_C7, RLB_CORR_C7_PRINTED = 0, 1, 2
 
 _STATUS = {0: "RLB_OK", 1: "RLB_EINVAL", 2: "RLB_ENOMEM", 3: "RLB_ECUDA", 4: "RLB_ENONPHYS", 5: "RLB_ETIMEOUT"}
 

@@ -21,7 +21,7 @@ struct rlb_handle {
   unsigned long long* d_bad = nullptr;   // smallest non-physical node index, ULLONG_MAX if none
   double* d_part = nullptr;              // reduction partials
   double* d_stage = nullptr;             // 6 x nodes FP64 staging for host field I/O
-  double* d_macro = nullptr;             // 4 x nodes FP64 fields for the C_7 gradients (RLB_CORR_C7)
+  double* d_macro = nullptr;             // 6 x nodes FP64 fields for the C_7 gradients (RLB_CORR_C7*)
   rlb::StepConst k{};
   long long steps = 0;
   std::string err;

@@ -334,7 +334,8 @@ __device__ __forceinline__ unsigned pull_d2q9(const double* __restrict__ src, co
 }
 
 // Fields of the pulled D2Q9 state for the C_7 gradients (Eq. 38): per node
-// c_s^2 sigma - P, gamma, sigma u_x^2, sigma u_x.
+// c_s^2 sigma - P, gamma, sigma u_x^2, sigma u_x, sigma u_y^2, sigma u_y.
+constexpr int kMacroD2Q9 = 6;
 __global__ void __launch_bounds__(kBlockX) k_macro_d2q9(const double* __restrict__ src, double* __restrict__ q,
                                                         Geo geo) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -344,15 +345,31 @@ __global__ void __launch_bounds__(kBlockX) k_macro_d2q9(const double* __restrict
   NodeMacro m;
   node_moments_d2q9<double>(f, g, dp, Sa, Sd, m);
   node_recover_fast(m);
-  const double su = m.sigma * m.ux;
+  const double sux = m.sigma * m.ux, suy = m.sigma * m.uy;
   q[node] = fma(1.0 / 3.0, m.sigma, -m.P);
   q[geo.plane + node] = 1.0 / sqrt(1.0 - m.u2);
-  q[2 * geo.plane + node] = su * m.ux;
-  q[3 * geo.plane + node] = su;
+  q[2 * geo.plane + node] = sux * m.ux;
+  q[3 * geo.plane + node] = sux;
+  q[4 * geo.plane + node] = suy * m.uy;
+  q[5 * geo.plane + node] = suy;
+}
+
+// One axis of the C_7 term (Eq. 38 for a flow along that axis): neighbours im, ip
+// of the node along the axis, u its velocity component, qa = q + 2 plane (x) or
+// q + 4 plane (y) the sigma u^2 / sigma u fields of that component.
+__device__ __forceinline__ double c7_axis(const double* __restrict__ q, const double* __restrict__ qa,
+                                          unsigned long long P, unsigned im, unsigned ip, double u, double sigma,
+                                          double gam, double theta, double kth) {
+  const double d1 = 0.5 * (q[ip] - q[im]);              // d(c_s^2 sigma - P)
+  const double d2 = 0.5 * (q[P + ip] - q[P + im]);      // d(gamma)
+  const double d3 = 0.5 * (qa[ip] - qa[im]);            // d(sigma u^2)
+  const double d4 = 0.5 * (qa[P + ip] - qa[P + im]);    // d(sigma u)
+  return 2.0 * (u * d1 - (sigma * (1.0 / 3.0)) * (u / gam) * d2 - u * d3) + kth * (u * u * theta * d4);
 }
 
 // D2Q9 (FP64): node (x, y) pulls link a from (x - c_x, y - c_y).  With CORR the
-// C_7 term of Eqs. 37-38 is added to the m_7 = p_xx moment of the result.
+// C_7 term of Eqs. 37-38, C_7 = E_x - E_y, is added to the m_7 = p_xx moment of the
+// result.
 template <bool MRT, bool QSEP, bool CORR, bool ETA = false>
 __global__ void __launch_bounds__(kBlockX) k_step_d2q9(const double* __restrict__ src, double* __restrict__ dst,
                                                        Geo geo, StepConst k, unsigned long long* __restrict__ bad,
@@ -366,18 +383,17 @@ __global__ void __launch_bounds__(kBlockX) k_step_d2q9(const double* __restrict_
   const bool b = node_collide_d2q9_f64<MRT, QSEP, ETA>(f, g, k, m);
   if (b) atomicMin(bad, (unsigned long long)node);
   if (CORR) {
-    // neighbours along x: a zero-gradient end reuses the edge node, a periodic axis wraps
-    const unsigned rowy = (unsigned)y * (unsigned)geo.nx;
+    // neighbours: a zero-gradient end reuses the edge node, a periodic axis wraps
+    const unsigned nx = (unsigned)geo.nx, rowy = (unsigned)y * nx;
     const unsigned xm = rowy + (unsigned)(x > 0 ? x - 1 : (geo.bcx ? 0 : geo.nx - 1));
     const unsigned xp = rowy + (unsigned)(x < geo.nx - 1 ? x + 1 : (geo.bcx ? geo.nx - 1 : 0));
+    const unsigned ym = (unsigned)(y > 0 ? y - 1 : (geo.bcy ? 0 : geo.ny - 1)) * nx + (unsigned)x;
+    const unsigned yp = (unsigned)(y < geo.ny - 1 ? y + 1 : (geo.bcy ? geo.ny - 1 : 0)) * nx + (unsigned)x;
     const unsigned long long P = geo.plane;
-    const double d1 = 0.5 * (q[xp] - q[xm]);                    // dx(c_s^2 sigma - P)
-    const double d2 = 0.5 * (q[P + xp] - q[P + xm]);            // dx(gamma)
-    const double d3 = 0.5 * (q[2 * P + xp] - q[2 * P + xm]);    // dx(sigma u^2)
-    const double d4 = 0.5 * (q[3 * P + xp] - q[3 * P + xm]);    // dx(sigma u)
-    const double u = m.ux, gam = q[P + node];
+    const double gam = q[P + node];
     const double theta = 1.0 + 1.0 / fma(4.0 * gam, gam, -1.0);   // e / P = 3
-    const double c7 = 2.0 * (u * d1 - (m.sigma * (1.0 / 3.0)) * (u / gam) * d2 - u * d3 + u * u * theta * d4);
+    const double c7 = c7_axis(q, q + 2 * P, P, xm, xp, m.ux, m.sigma, gam, theta, k.c7_theta) -
+                      c7_axis(q, q + 4 * P, P, ym, yp, m.uy, m.sigma, gam, theta, k.c7_theta);
     // m_7 = p_xx (row c_x^2 - c_y^2, norm 4): (1 - s_7/2) C_7 spread over the axis links
     const double dq = 0.25 * (1.0 - 0.5 * k.omv) * c7;
     g[1] += dq;
@@ -462,7 +478,7 @@ cudaError_t launch_step(rlb_handle* h, const void* src, void* dst, cudaStream_t 
       if (!mrt2) k_step_d2q9<false, false, false, true><<<grid2, bx, 0, st>>>(s2, d2, geo, h->k, h->d_bad, nullptr);
       else if (!q2) k_step_d2q9<true, false, false, true><<<grid2, bx, 0, st>>>(s2, d2, geo, h->k, h->d_bad, nullptr);
       else k_step_d2q9<true, true, false, true><<<grid2, bx, 0, st>>>(s2, d2, geo, h->k, h->d_bad, nullptr);
-    } else if (h->cfg.correction == RLB_CORR_C7) {
+    } else if (h->cfg.correction != RLB_CORR_NONE) {
       k_macro_d2q9<<<grid2, bx, 0, st>>>(s2, h->d_macro, geo);
       if (!q2) k_step_d2q9<true, false, true><<<grid2, bx, 0, st>>>(s2, d2, geo, h->k, h->d_bad, h->d_macro);
       else k_step_d2q9<true, true, true><<<grid2, bx, 0, st>>>(s2, d2, geo, h->k, h->d_bad, h->d_macro);
@@ -580,8 +596,9 @@ extern "C" int rlb_create(const rlb_config* cfg, rlb_handle** out) {
     return fail(nullptr, RLB_EINVAL, "lattice must be RLB_D3Q19 or RLB_D2Q9");
   if (cfg->lattice == RLB_D2Q9 && (cfg->nz != 1 || cfg->precision != RLB_FP64))
     return fail(nullptr, RLB_EINVAL, "RLB_D2Q9 needs nz == 1 and RLB_FP64");
-  if (cfg->correction != RLB_CORR_NONE &&
-      (cfg->correction != RLB_CORR_C7 || cfg->lattice != RLB_D2Q9 || cfg->collision != RLB_MRT))
+  if (cfg->correction != RLB_CORR_NONE && cfg->correction != RLB_CORR_C7 && cfg->correction != RLB_CORR_C7_PRINTED)
+    return fail(nullptr, RLB_EINVAL, "unknown correction");
+  if (cfg->correction != RLB_CORR_NONE && (cfg->lattice != RLB_D2Q9 || cfg->collision != RLB_MRT))
     return fail(nullptr, RLB_EINVAL, "RLB_CORR_C7 needs RLB_D2Q9 and RLB_MRT");
   if (cfg->eos != RLB_EOS_ULTRAREL) return fail(nullptr, RLB_EINVAL, "only RLB_EOS_ULTRAREL (P = e/3) is supported");
   if (cfg->collision != RLB_BGK && cfg->collision != RLB_MRT) return fail(nullptr, RLB_EINVAL, "unknown collision");
@@ -620,6 +637,7 @@ extern "C" int rlb_create(const rlb_config* cfg, rlb_handle** out) {
   h->k.a_e = cfg->tau_e;
   h->k.a_p = cfg->tau_eps;
   h->k.a_q = cfg->tau_q > 0 ? cfg->tau_q : 1.0;
+  h->k.c7_theta = cfg->correction == RLB_CORR_C7_PRINTED ? 2.0 : 1.0;
   cudaGetDevice(&h->device);
   const size_t bytes = 2 * (size_t)h->Q * h->nodes * h->esize;
   for (int i = 0; i < 2; ++i) {
@@ -629,7 +647,8 @@ extern "C" int rlb_create(const rlb_config* cfg, rlb_handle** out) {
       return fail(nullptr, RLB_ENOMEM, "cannot allocate the two lattices");
     }
   }
-  if (cfg->correction == RLB_CORR_C7 && cudaMalloc(&h->d_macro, 4 * h->nodes * sizeof(double)) != cudaSuccess) {
+  if (cfg->correction != RLB_CORR_NONE &&
+      cudaMalloc(&h->d_macro, kMacroD2Q9 * h->nodes * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     h->d_macro = nullptr;
     rlb_destroy(h);

@@ -10,6 +10,9 @@
 // device array of fixed size, so it calls no cudaMalloc, cudaFree or allocating
 // library routine.
 //
+// It takes D3Q19 states only (38 values per node): the kernel reads 19 f and 19
+// g planes and cannot tell a D2Q9 state (18 values per node) from its size.
+//
 // The scratch array lives in every GPU that loads librlb until the process
 // exits.  All calls share it and it keeps the previous call's contents; each
 // call overwrites every partial it later reads, so nothing needs clearing, but

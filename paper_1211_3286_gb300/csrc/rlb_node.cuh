@@ -34,8 +34,9 @@
 //
 // Arithmetic variants in this file:
 //   node_collide_fx (and the warp-role kernel built from its parts): FP64
-//     populations, per-link work in 64-bit block fixed point on the integer
-//     pipes, recovery in FP64 -- the FP64 step with constant relaxation times;
+//     populations; sums, recovery (fx_recover) and per-link work in 64-bit
+//     block fixed point on the integer pipes, each output rounded once to FP64
+//     -- the FP64 step with constant relaxation times;
 //   node_collide_f64: the same update in FP64 arithmetic -- the fixed-eta/s
 //     mode, whose relaxation times vary per node;
 //   node_collide_f32s: FP32 population storage, exact sums, FP64 recovery,
@@ -88,6 +89,8 @@ struct StepConst {
   // below 2^63)
   unsigned long long Om_f, Om_v;
   long long CE, CP, CQ;
+  // coefficient of the theta term of the C_7 correction (Eq. 38): 1 (Eq. A17) or 2 (as printed)
+  double c7_theta;
 };
 
 // q = 19 (D3Q19: weights 1/3, 1/18, 1/36; MRT row norms e 2394, eps 252, q 40) or
@@ -886,7 +889,7 @@ __device__ __forceinline__ void fx_f_relax(const FState& s, const UFix& u, const
   relax_links<RLB_FX_OUT_F, false>(s.F, q, Om, c, c, dq0, s.Ef, f);
 }
 
-// FP64 node collide on the integer pipe: moments, recovery (FP64), equilibria, BGK f,
+// FP64 node collide on the integer pipe: moments, recovery (fixed point), equilibria, BGK f,
 // BGK / MRT g.  Same contract as node_collide_f64 with constant relaxation times; each
 // link agrees with it to a few units of 2^-56 of the node's largest population.
 template <bool MRT, bool QSEP>

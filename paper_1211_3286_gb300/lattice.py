@@ -15,6 +15,10 @@ _BC = {"periodic": L.RLB_PERIODIC, "zero_gradient": L.RLB_ZERO_GRADIENT}
 _COLL = {"bgk": L.RLB_BGK, "mrt": L.RLB_MRT}
 _PREC = {"fp64": L.RLB_FP64, "fp32": L.RLB_FP32_STORAGE}
 _LAT = {"d3q19": L.RLB_D3Q19, "d2q9": L.RLB_D2Q9}
+# the C_7 term of Eqs. 37-38: True / "c7" (theta term with Eq. A17's coefficient 1),
+# "c7_printed" (Eq. 38 as printed, coefficient 2)
+_CORR = {False: L.RLB_CORR_NONE, None: L.RLB_CORR_NONE, True: L.RLB_CORR_C7, "c7": L.RLB_CORR_C7,
+         "c7_printed": L.RLB_CORR_C7_PRINTED}
 
 
 def _where(t: torch.Tensor):
@@ -43,7 +47,8 @@ def _f64(t):
 
 
 class Lattice:
-    """A (nz, ny, nx) D3Q19 lattice with f and g populations on the current GPU."""
+    """A (nz, ny, nx) D3Q19 (or D2Q9, nz = 1) lattice with f and g populations on the
+    current GPU."""
 
     def __init__(self, shape, collision="mrt", tau_f=0.9, tau_v=0.9, tau_e=0.9, tau_eps=0.9, tau_q=0.0,
                  bc=("periodic", "periodic", "periodic"), precision="fp64", stream=None, lattice="d3q19",
@@ -60,7 +65,7 @@ class Lattice:
         for a in range(3):
             cfg.bc[a] = _BC[bc[a]]
         cfg.precision = _PREC[precision]
-        cfg.correction = L.RLB_CORR_C7 if correction else L.RLB_CORR_NONE
+        cfg.correction = _CORR[correction]
         cfg.eta_over_s = eta_over_s
         if stream is None and torch.cuda.is_available():
             stream = torch.cuda.current_stream()

@@ -50,6 +50,7 @@ def _cfg(**kw):
     for a in range(3):
         c.bc[a] = L.RLB_PERIODIC
     c.precision = kw.get("precision", L.RLB_FP64)
+    c.correction = kw.get("correction", L.RLB_CORR_NONE)
     return c
 
 
@@ -58,6 +59,8 @@ def _cfg(**kw):
     (dict(lattice=9, precision=1), "D2Q9"), (dict(collision=7), "collision"),
     (dict(precision=5), "precision"), (dict(taus=(0.5, 0.9, 0.55, 0.8, 0.0)), "tau_f"),
     (dict(taus=(0.9, 0.9, 0.4, 0.8, 0.0)), "tau_e"), (dict(taus=(0.9, 0.9, 0.55, 0.8, 0.3)), "tau_q"),
+    (dict(lattice=9, correction=3), "unknown correction"), (dict(correction=1), "needs RLB_D2Q9"),
+    (dict(lattice=9, collision=0, correction=2), "needs RLB_D2Q9"),
 ])
 def test_create_rejects_invalid_config_before_touching_the_gpu(lib, kw, what):
     from paper_1211_3286_gb300 import _lib as L

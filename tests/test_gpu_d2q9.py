@@ -87,11 +87,12 @@ def test_d2q9_rejects_invalid_setups():
     lat.close()
 
 
-@pytest.mark.parametrize("bcx", ["zero_gradient", "periodic"])
-def test_d2q9_c7_correction(bcx):
-    """Eqs. 37-38 (RLB_CORR_C7): the moderately relativistic shock (n = P/T) on a 4-wide
-    tube with tau_v = 3, tau_e = tau_eps = 0.5 + (tau_v - 0.5)/30, corrected m_7;
-    FP64 parity with the oracle's corrected collision."""
+@pytest.mark.parametrize("bcx,corr", [("zero_gradient", "c7"), ("periodic", "c7"), ("zero_gradient", "c7_printed")])
+def test_d2q9_c7_correction(bcx, corr):
+    """Eqs. 37-38 (RLB_CORR_C7, and RLB_CORR_C7_PRINTED with Eq. 38's theta term as
+    printed): the moderately relativistic shock (n = P/T) on a 4-wide tube along x with
+    tau_v = 3, tau_e = tau_eps = 0.5 + (tau_v - 0.5)/30, corrected m_7; FP64 parity
+    with the oracle's corrected collision."""
     from paper_1211_3286_gb300.lattice import Lattice
     L, T = 300, 200
     e, ux, uy, uz, n = (torch.from_numpy(a) for a in I.shock_tube(L, **I.MODERATE))
@@ -100,13 +101,13 @@ def test_d2q9_c7_correction(bcx):
     te = 0.5 + 2.5 / 30.0
     bc = (bcx, "periodic", "periodic")
     lat = Lattice((1, 4, L), collision="mrt", tau_f=3.0, tau_v=3.0, tau_e=te, tau_eps=te, bc=bc, lattice="d2q9",
-                  correction=True)
+                  correction=corr)
     lat.set_fields(e2.cuda(), z.cuda(), z.cuda(), z.cuda(), n2.cuda())
     lat.step(T)
     gpu = lat.fields("cuda")
     lat.close()
     prm = O.Params(collision="mrt", tau_f=3.0, tau_v=3.0, tau_e=te, tau_eps=te, bc=oracle_bc(bc), lattice="d2q9",
-                   correction=True)
+                   correction=True, c7_theta=2.0 if corr == "c7_printed" else 1.0)
     f, g = O.run(*O.init_populations(e2, torch.stack([z, z, z]), n2, "d2q9"), prm, T)
     ref = oracle_fields(f, g)
     err = field_errors(gpu, ref)
@@ -115,6 +116,55 @@ def test_d2q9_c7_correction(bcx):
     fu, gu = O.run(*O.init_populations(e2, torch.stack([z, z, z]), n2, "d2q9"),
                    O.dataclasses.replace(prm, correction=False), T)
     assert float((O.fields(fu, gu).P - ref["P"]).abs().max()) > 1e-6 * float(ref["P"].max())
+
+
+def _paper_tube(axis, steps, corr="c7"):
+    """Sec. V.B geometry: 4 x 800, the moderately relativistic shock (n = P/T), open
+    ends along the tube, periodic across, tau_v = 3, a = 1/30 (Case D), C_7 on; the
+    tube along x (axis 0) or along y (axis 1, the paper's orientation)."""
+    from paper_1211_3286_gb300.lattice import Lattice
+    L = 800
+    e, ux, uy, uz, n = (torch.from_numpy(a) for a in I.shock_tube(L, **I.MODERATE))
+    shape = (1, 4, L) if axis == 0 else (1, L, 4)
+    pro = (lambda q: q.reshape(1, 1, L).expand(shape)) if axis == 0 else (lambda q: q.reshape(1, L, 1).expand(shape))
+    e2, n2 = pro(e).contiguous(), pro(n).contiguous()
+    z = torch.zeros(shape, dtype=torch.float64)
+    te = 0.5 + 2.5 / 30.0
+    bc = ("zero_gradient", "periodic", "periodic") if axis == 0 else ("periodic", "zero_gradient", "periodic")
+    lat = Lattice(shape, collision="mrt", tau_f=3.0, tau_v=3.0, tau_e=te, tau_eps=te, bc=bc, lattice="d2q9",
+                  correction=corr)
+    lat.set_fields(e2.cuda(), z.cuda(), z.cuda(), z.cuda(), n2.cuda())
+    lat.step(steps)
+    lat.check()
+    gpu = lat.fields("cpu")
+    lat.close()
+    return gpu, (e2, z, n2, bc, te)
+
+
+def test_d2q9_c7_paper_geometry_along_y():
+    """The paper's own orientation (flow along the second axis, 4 x 800, t = 400) with
+    C_7: FP64 parity with the oracle."""
+    T = 400
+    gpu, (e2, z, n2, bc, te) = _paper_tube(1, T)
+    prm = O.Params(collision="mrt", tau_f=3.0, tau_v=3.0, tau_e=te, tau_eps=te, bc=oracle_bc(bc), lattice="d2q9",
+                   correction=True)
+    f, g = O.run(*O.init_populations(e2, torch.stack([z, z, z]), n2, "d2q9"), prm, T)
+    err = field_errors(gpu, oracle_fields(f, g))
+    assert max(err.values()) < TOL64, err
+    assert float(gpu["uy"].abs().max()) > 0.5
+
+
+def test_d2q9_c7_tube_along_y_is_the_x_tube_relabelled():
+    """GPU runs of the tube along x and along y (C_7 on, 400 steps) agree under the
+    swap of axes to round-off."""
+    a, _ = _paper_tube(0, 400)
+    b, _ = _paper_tube(1, 400)
+    for k in ("e", "P", "n"):
+        x, y = a[k][0], b[k][0].transpose(0, 1)
+        assert float((x - y).abs().max()) <= 1e-11 * float(x.abs().max()), k
+    umax = float(a["ux"].abs().max())
+    assert float((a["ux"][0] - b["uy"][0].transpose(0, 1)).abs().max()) <= 1e-11 * umax
+    assert float(b["ux"].abs().max()) <= 1e-12 * umax and float(a["uy"].abs().max()) <= 1e-12 * umax
 
 
 def test_c7_rejected_outside_d2q9_mrt():

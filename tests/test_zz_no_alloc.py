@@ -5,8 +5,10 @@ GPU memory is all handed to a pool reserved at start-up, monitoring code that
 runs after an out-of-memory failure, loops that must not stall on cudaMalloc's
 device synchronisation) use this call; its only scratch is a fixed file-scope
 device array.  The test calls it through the C ABI twice in a row on the same
-state and checks both results against rlb_conserved_totals, within the 1e-13
-relative tolerance the conservation tests use.  This file is collected last.
+state, on a lattice that fills three of the call's 65,536-node reduction slots and
+a ragged fourth, and checks both results against rlb_conserved_totals and against
+the oracle's conserved_totals of the same state, within the 1e-13 relative
+tolerance the conservation tests use.  This file is collected last.
 """
 import ctypes
 
@@ -26,7 +28,8 @@ def test_noalloc_totals_match_handle_totals_twice(precision):
     from paper_1211_3286_gb300 import build
     from paper_1211_3286_gb300.lattice import Lattice
     build.build()
-    shape = (12, 17, 131)
+    import oracle.rlb_oracle as O
+    shape = (7, 23, 1301)       # 209,461 nodes: three full 65,536-node slots and a ragged fourth
     e, ux, uy, uz, n = I.periodic_box(None, seed=31, shape=shape)
     lat = Lattice(shape, collision="mrt", tau_f=0.9, tau_v=0.9, tau_e=0.55, tau_eps=0.8, precision=precision)
     lat.set_fields(e.cuda(), ux.cuda(), uy.cuda(), uz.cuda(), n.cuda())
@@ -35,6 +38,9 @@ def test_noalloc_totals_match_handle_totals_twice(precision):
     state = lat.state("cuda")
     torch.cuda.synchronize()
     nodes = shape[0] * shape[1] * shape[2]
+    assert nodes > 3 * 65536 and nodes % 65536
+    st = state.cpu().to(torch.float64)
+    ref = O.conserved_totals(st[:19], st[19:]).tolist()
     prec = L.RLB_FP64 if precision == "fp64" else L.RLB_FP32_STORAGE
     scale = [abs(want[0])] + [abs(want[1])] * 4
     stream = torch.cuda.current_stream().cuda_stream
@@ -52,6 +58,7 @@ def test_noalloc_totals_match_handle_totals_twice(precision):
                 torch.cuda.synchronize()
                 got = dout.cpu().tolist()
             assert max(abs(a - b) / s for a, b, s in zip(got, want, scale)) < 1e-13, (got, want)
+            assert max(abs(a - b) / s for a, b, s in zip(got, ref, scale)) < 1e-13, (got, ref)
     lat.close()
 
 
