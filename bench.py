@@ -10,6 +10,14 @@ Metric: MLUPS (million lattice-node updates per second), higher is better.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload box256|box512_fp32]
 
+The metric has two halves, FP64 and FP32 population storage.  The default run
+times the 256^3 FP64 box and then the 512^3 FP32-storage box of the same fields
+and relaxation times, and nests the second in the same line as ``fp32_storage``
+(its own timing, roofline, clocks, end-to-end figure and per-field error against
+the FP64 path).  Each box is timed as repeated regions of exactly K steps (at
+least --min-repeats of them and --min-seconds of device time); the median region
+is reported, with the spread.
+
 Prints one JSON line.  ``--impl reference`` times the CPU oracle (the plain FP64
 statement of the scheme) on the host cores over a bounded sample of the same
 workload.  Under torchrun every rank runs its own replica (the lattices are
@@ -66,11 +74,10 @@ DEFAULT_STEPS = {"box256": 500, "box128": 500, "box128_fp32": 500, "box512_fp32"
 
 # DRAM bytes (read + write) per node update of the step kernel, from ncu captures of the
 # 128^3 box with the same kernel (the 256^3 / 512^3 lattices exceed the capture size
-# rule); traffic per launch = bytes per update x nodes.  profiles/k_step_box128_f32.md:
-# 587.7 MB / 2,097,152.  None where the kernel changed since its capture (the FP64 step:
-# profiles/k_step_ws_box128_f64.md measured 1282.3 MB / 2,097,152 before its loads
-# took the L1::no_allocate hint).
-NCU_BYTES_PER_UPDATE = {"fp64": None, "fp32": 587.74784e6 / 2097152}
+# rule); traffic per launch = bytes per update x nodes.  profiles/k_step_ws_box128_f64.md:
+# 638.9 MB read + 626.0 MB written / 2,097,152; profiles/k_step_box128_f32.md: 587.7 MB /
+# 2,097,152.
+NCU_BYTES_PER_UPDATE = {"fp64": (638868224 + 626036736) / 2097152, "fp32": 587.74784e6 / 2097152}
 # k_tubes on the 1024-tube sweep (profiles/k_tubes_sweep1024_fp32.md): 52.04 GB over
 # 1,719,757 nodes x 200 steps
 NCU_BYTES_PER_UPDATE_TUBES = 52.044659e9 / (1719757 * 200)
@@ -185,6 +192,8 @@ def cpu_baseline(seconds_budget=15.0):
     import oracle.rlb_oracle as O
     from paper_1211_3286_gb300 import inputs as I
     n = 48
+    affinity = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    torch.set_num_threads(affinity)
     e, ux, uy, uz, nn = I.periodic_box(None, shape=(n, n, n))
     prm = O.Params(collision="mrt", **TAUS)
     f, g = O.init_populations(e, torch.stack([ux, uy, uz]), nn)
@@ -195,6 +204,8 @@ def cpu_baseline(seconds_budget=15.0):
         steps += 1
     dt = time.perf_counter() - t0
     return {"value": n ** 3 * steps / dt / 1e6, "unit": "MLUPS", "cores": torch.get_num_threads(),
+            "host_cpus": os.cpu_count(), "affinity_cpus": affinity,
+            "cores_note": "cores = torch CPU threads the oracle ran on, set to the process's CPU affinity",
             "cpu_model": _cpu_model(), "kind": "oracle",
             "sample": "%d^3 MRT box, %d steps, same generator and taus, FP64 oracle" % (n, steps),
             "seconds": round(dt, 2)}
@@ -380,22 +391,15 @@ def run_adjoint(args, dist, rank, ws, local):
         print(json.dumps(line))
 
 
-def run_ours(args):
-    dist, rank, ws = _dist()
-    if not torch.cuda.is_available():
-        raise SystemExit("bench.py needs a CUDA GPU (librlb has no CPU path)")
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    import __graft_entry__
-    __graft_entry__.build()
+def time_box(args, wl, steps, dist, ws, local, min_repeats=5, min_seconds=2.0, e2e=True):
+    """Time one box workload: warm-up, then repeated timed regions of exactly
+    ``steps`` launches each (at least ``min_repeats`` of them and at least
+    ``min_seconds`` of device time in total), each bracketed by a barrier and a
+    device synchronisation, with CUDA events on the library's stream.  Returns
+    the median region, its spread, the clocks sampled over all regions and the
+    end-to-end (host buffers) measurement."""
     from paper_1211_3286_gb300 import inputs as I
     from paper_1211_3286_gb300.lattice import Lattice
-
-    if args.workload in ("tubes", "tubes_small"):
-        return run_tubes(args, dist, rank, ws, local)
-    if args.workload == "adjoint":
-        return run_adjoint(args, dist, rank, ws, local)
-    wl = WORKLOADS[args.workload]
     N = wl["N"]
     nodes = N ** 3
     stream = torch.cuda.Stream()
@@ -406,30 +410,32 @@ def run_ours(args):
     del e, ux, uy, uz, n
     torch.cuda.synchronize()
 
-    # warm-up
     lat.step(args.warmup)
     lat.check()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize()
+    regions = []
     with ClockSampler(local) as cs:
-        ev0.record(stream)
-        lat.step(args.steps)
-        ev1.record(stream)
-        torch.cuda.synchronize()
+        while len(regions) < min_repeats or sum(regions) < min_seconds * 1e3:
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            if dist is not None:
+                dist.barrier()
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            lat.step(steps)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            regions.append(reduce_max(ev0.elapsed_time(ev1), dist))
+            if len(regions) >= 200:
+                break
     if dist is not None:
         dist.barrier()
     lat.check()
-    ms = reduce_max(ev0.elapsed_time(ev1), dist)
+    ms = statistics.median(regions)
     clocks = cs.summary()
-    per_launch_s = ms / 1e3 / args.steps
-    mlups = whole_job_rate(nodes * args.steps, ws, ms / 1e3)
 
     # end to end through the C ABI with pinned host buffers: upload the initial
     # fields, run the steps, read the final fields back
-    e2e = None
-    if not args.no_e2e:
+    out_e2e = None
+    if e2e:
         from paper_1211_3286_gb300 import _lib as L
         import ctypes
         hf = [t.cpu().pin_memory() for t in I.periodic_box(N, device="cuda")]
@@ -443,50 +449,98 @@ def run_ours(args):
             dist.barrier()
         t0 = time.perf_counter()
         lat.set_fields(*hf)
-        lat.step(args.steps)
+        lat.step(steps)
         L.rlb_get_fields(lat.handle, *[ctypes.c_void_p(o.data_ptr()) for o in outs], L.RLB_HOST)
         dt = reduce_max(time.perf_counter() - t0, dist)
-        e2e = {"value": whole_job_rate(nodes * args.steps, ws, dt), "unit": "MLUPS",
-               "h2d_bytes_per_step": 5 * nodes * 8 / args.steps, "d2h_bytes_per_step": 6 * nodes * 8 / args.steps,
-               "what": "rlb_set_fields(host) + rlb_step(K) + rlb_get_fields(host), pinned buffers"}
+        out_e2e = {"value": whole_job_rate(nodes * steps, ws, dt), "unit": "MLUPS",
+                   "h2d_bytes_per_step": 5 * nodes * 8 / steps, "d2h_bytes_per_step": 6 * nodes * 8 / steps,
+                   "what": "rlb_set_fields(host) + rlb_step(K) + rlb_get_fields(host), pinned buffers"}
+        del hf, outs
     lat.close()
+    del lat
+    torch.cuda.empty_cache()
 
-    # FP32 storage: per-field error of the final fields against the FP64 path on the
-    # same initial fields and step count (outside the timed region)
-    err = None
-    if wl["precision"] == "fp32" and not args.no_error:
-        err = fp32_error_vs_fp64(N, args.steps, stream)
-
+    per_launch_s = ms / 1e3 / steps
     hbm_peak, peak_kind = _peaks()
     gbs = wl["bytes_per_update"] * nodes / per_launch_s / 1e9
     nb = NCU_BYTES_PER_UPDATE.get(wl["precision"])
     traffic = None if nb is None else nb * nodes
     hbm = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
-           "traffic": traffic, "peak_kind": peak_kind}
+           "traffic": traffic, "peak_kind": peak_kind,
+           "algorithmic_bytes": "%d B per node update x %d nodes per launch" % (wl["bytes_per_update"], nodes)}
     roof = hbm
-    if wl["precision"] == "fp64":
-        # The FP64 pipe (152 SMs x 2 instructions per clock x 2.07 GHz) carries the
-        # recovery and the int64 -> FP64 roundings; the roofline reported is the
-        # bound with the larger fraction.
-        fp64_peak = 152 * 2 * 2.07
-        gops = FP64_OPS_PER_UPDATE * nodes / per_launch_s / 1e9
-        alu = {"bound": "alu", "achieved": gops, "peak": fp64_peak, "unit": "G FP64-pipe op/s",
-               "frac": gops / fp64_peak, "traffic": traffic,
-               "peak_kind": "derived: 152 SM x 2 FP64 op/clk x 2.07 GHz (measured 2.05 DFMA/clk/SM)",
-               "hbm_frac": gbs / hbm_peak}
-        if alu["frac"] > hbm["frac"]:
-            roof = alu
+    fp64_ops = FP64_OPS_PER_UPDATE if wl["precision"] == "fp64" else FP64_OPS_PER_UPDATE_F32S
+    # The FP64 pipe (152 SMs x 2 instructions per clock x 2.07 GHz) carries the
+    # int64 -> FP64 roundings (and, with FP32 storage, the recovery); the roofline
+    # reported is the bound with the larger fraction.
+    fp64_peak = 152 * 2 * 2.07
+    gops = fp64_ops * nodes / per_launch_s / 1e9
+    alu = {"bound": "alu", "achieved": gops, "peak": fp64_peak, "unit": "G FP64-pipe op/s",
+           "frac": gops / fp64_peak, "traffic": traffic,
+           "peak_kind": "derived: 152 SM x 2 FP64 op/clk x 2.07 GHz (measured 2.05 DFMA/clk/SM)",
+           "hbm_frac": gbs / hbm_peak}
+    if alu["frac"] > hbm["frac"]:
+        roof = alu
+    per_step = sorted(r / steps for r in regions)
+    return {"value": whole_job_rate(nodes * steps, ws, ms / 1e3), "ms_per_step": ms / steps,
+            "ms_per_step_spread": [per_step[0], per_step[-1]], "repeats": len(regions),
+            "ms_per_step_x_sm_mhz": (ms / steps * clocks["sm_mhz"]) if clocks.get("sm_mhz") else None,
+            "nodes": nodes, "roofline": roof, "hbm_roofline": hbm, "clocks": clocks, "e2e": out_e2e,
+            "gpu_launches": steps * len(regions)}
+
+
+def run_ours(args):
+    dist, rank, ws = _dist()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (librlb has no CPU path)")
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+
+    if args.workload in ("tubes", "tubes_small"):
+        return run_tubes(args, dist, rank, ws, local)
+    if args.workload == "adjoint":
+        return run_adjoint(args, dist, rank, ws, local)
+    wl = WORKLOADS[args.workload]
+    r = time_box(args, wl, args.steps, dist, ws, local, min_repeats=args.min_repeats,
+                 min_seconds=args.min_seconds, e2e=not args.no_e2e)
+
+    # FP32 storage: per-field error of the final fields against the FP64 path on the
+    # same initial fields and step count (outside the timed region)
+    err = None
+    if wl["precision"] == "fp32" and not args.no_error:
+        err = fp32_error_vs_fp64(wl["N"], args.steps, torch.cuda.Stream())
+
+    # the metric's second half: the FP32-storage variant of the same box, 512^3,
+    # timed the same way after the FP64 lattice is freed
+    f32 = None
+    if args.workload == "box256" and not args.no_fp32_storage:
+        w32 = WORKLOADS["box512_fp32"]
+        k32 = args.steps if args.steps_given else DEFAULT_STEPS["box512_fp32"]
+        f32 = time_box(args, w32, k32, dist, ws, local, min_repeats=args.min_repeats,
+                       min_seconds=args.min_seconds, e2e=not args.no_e2e)
+        f32 = {"workload": w32["desc"], "metric": "MLUPS", "unit": "MLUPS", "steps": k32, "dtype": w32["dtype"],
+               **f32, "speedup_vs_fp64": f32["value"] / r["value"]}
+        if not args.no_error:
+            f32["error_vs_fp64"] = fp32_error_vs_fp64(w32["N"], k32, torch.cuda.Stream())
+
     if rank == 0:
-        line = {"metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": wl["dtype"], "data": "synthetic",
-                "config": {"workload": wl["desc"], "nodes": nodes, "l2": "lattice (%.1f GB) larger than L2"
-                           % (2 * 38 * nodes * (8 if wl["precision"] == "fp64" else 4) / 1e9),
-                           "parallelism": "replicas" if ws > 1 else "single"},
-                "roofline": roof, "hbm_roofline": hbm, "clocks": clocks, "e2e": e2e,
-                "gpu_launches": args.steps}
+        line = {"metric": "MLUPS", "value": r["value"], "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": wl["dtype"], "data": "synthetic",
+                "config": {"workload": wl["desc"], "nodes": r["nodes"], "l2": "lattice (%.1f GB) larger than L2"
+                           % (2 * 38 * r["nodes"] * (8 if wl["precision"] == "fp64" else 4) / 1e9),
+                           "parallelism": "replicas" if ws > 1 else "single",
+                           "timing": "median of %d timed regions of %d steps each" % (r["repeats"], args.steps)},
+                "ms_per_step_spread": r["ms_per_step_spread"], "repeats": r["repeats"],
+                "ms_per_step_x_sm_mhz": r["ms_per_step_x_sm_mhz"],
+                "roofline": r["roofline"], "hbm_roofline": r["hbm_roofline"], "clocks": r["clocks"],
+                "e2e": r["e2e"], "gpu_launches": r["gpu_launches"]}
         if err is not None:
             line["error_vs_fp64"] = err
+        if f32 is not None:
+            line["fp32_storage"] = f32
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline(args.ref_seconds)
         print(json.dumps(line))
@@ -531,9 +585,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-error", action="store_true",
                     help="skip the FP32-storage error run against the FP64 path")
+    ap.add_argument("--min-repeats", type=int, default=5,
+                    help="box workloads: at least this many timed regions of --steps steps (median reported)")
+    ap.add_argument("--min-seconds", type=float, default=2.0,
+                    help="box workloads: repeat timed regions until this much device time has passed")
+    ap.add_argument("--no-fp32-storage", action="store_true",
+                    help="default workload only: skip the nested FP32-storage 512^3 box")
     ap.add_argument("--ref-seconds", type=float, default=20.0,
                     help="CPU budget of the oracle sample (reference arm and cpu_baseline)")
     args = ap.parse_args()
+    args.steps_given = args.steps is not None
     if args.steps is None:
         args.steps = DEFAULT_STEPS.get(args.workload, 500)
     if args.warmup < 3:
