@@ -586,11 +586,14 @@ __device__ __forceinline__ long long to_fixed_pos(double x, int Er) {
   return (long long)(((unsigned long long)(th >> r) << 32) | __funnelshift_r(tl, th, r));
 }
 
-// The same through the FP64 pipe's int64 conversion (round to nearest even).
+// The same through the FP64 pipe's int64 conversion (round to nearest even) of K | 1:
+// setting the lowest bit keeps the converted value away from zero, so the exponent
+// can be rebased without a zero test.  It moves K by at most one grid unit (2^-56 of
+// the node's largest population, the grid's own resolution): an exact zero comes out
+// as that one unit, and a tie in the rounding of a wide K rounds away from zero.
 __device__ __forceinline__ double from_fixed_dp(long long K, int E) {
-  const double d = __ll2double_rn(K);
-  const int hi = __double2hiint(d);   // 0 exactly when K = 0 (then the low word is 0 too)
-  return __hiloint2double(hi ? hi + (int)((unsigned)(E - 1079) << 20) : 0, __double2loint(d));
+  const double d = __ll2double_rn(K | 1ll);
+  return __hiloint2double(__double2hiint(d) + (int)((unsigned)(E - 1079) << 20), __double2loint(d));
 }
 // K * 2^(E - 1079) rounded to the nearest double (ties to even) by integer bit
 // assembly for 2^32 <= K < 2^63, the range of a population near its node's largest;
@@ -619,7 +622,6 @@ __device__ __forceinline__ long long relax(long long X, long long Xeq, unsigned 
   const unsigned long long y = (unsigned long long)(X - Xeq) << 1;
   return X - (long long)mulhi(y ^ kSignBit, Om) + c;
 }
-
 // Per-distribution equilibrium pieces on its grid (Eqs. 7-9 split per link pair):
 //   axis pair i:   ev = KA + X_i,                          od = Z_i
 //   diagonal i,j:  ev = KA/2 + (X_i + X_j)/2 +- Y_ij,       od = (Z_i +- Z_j)/2

@@ -164,3 +164,25 @@ def test_config5_1600_nodes_4000_steps_vs_central_differences():
         ad_e.append(float(de0[0, 0, j]))
     fd_e, ad_e = torch.tensor(fd_e), torch.tensor(ad_e)
     assert float((fd_e - ad_e).abs().max() / ad_e.abs().max()) <= 1e-6, (fd_e, ad_e)
+
+
+@pytest.mark.parametrize("shape, kind, T, K", [
+    ((1, 1, 400), "tube", 400, 100),     # four lanes per node (k_adj_step_quad), 4 segments
+    ((1, 1, 1600), "tube", 200, 50),     # four lanes per node, 4 segments
+    ((4, 100, 100), "box", 12, 4),       # one thread per node (k_adj_step: > 38,912 nodes), 3 segments
+])
+def test_adjoint_matches_oracle_at_mid_size(shape, kind, T, K):
+    """MRT (0.9, 0.55, 0.8) gradients against the oracle's exact discrete gradient on
+    lattices where the checkpoint segments span many steps: J to 1e-9, d tau and
+    d e0 to 1e-8 (normwise).  The misfit is built from P - P* ~ 1e-3 P, so the 1e-13
+    agreement of the forward fields becomes ~1e-10 in J and its gradient."""
+    taus = (0.9, 0.55, 0.8)
+    bc = ZG if kind == "tube" else ("periodic",) * 3
+    e, u, n, tgt = _case(shape, kind, 54, taus, "mrt", bc, T)
+    loss, dtau, de0 = _gpu_grad(e, u, n, tgt, taus, "mrt", bc, T, K=K)
+    prm = O.Params(collision="mrt", tau_f=taus[0], tau_v=taus[0], tau_e=taus[1], tau_eps=taus[2], bc=_obc(bc))
+    lref, dref, eref = O.misfit_and_gradient(e, u, n, prm, T, tgt.P, tgt.u)
+    assert abs(loss - lref) <= 1e-9 * abs(lref), (loss, lref)
+    assert float((dtau - dref).abs().max() / dref.abs().max()) <= 1e-8, (dtau, dref)
+    err = float((de0.cpu() - eref).abs().max() / eref.abs().max())
+    assert err <= 1e-8, err

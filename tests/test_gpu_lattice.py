@@ -435,3 +435,33 @@ def test_eta_over_s_relaxation_fig1(eta_s, tau_f):
     ref = oracle_fields(*O.run(*O.init_populations(e, torch.stack([ux, uy, uz]), n), prm, T))
     err = field_errors(gpu, ref)
     assert max(err.values()) < TOL64, err
+
+
+def test_fp64_step_per_population_precision_64_cubed():
+    """Element-by-element precision of the FP64 step's stored populations on the 3-D
+    MRT box workload (64^3, max|u| = 0.3, 50 steps) against the oracle.  The step works
+    on each node's fixed-point grid, one unit = 2^-56 of the node's largest population
+    of that distribution (M), a few units per step; the oracle rounds each operation in
+    FP64 (2^-53 of the value).  Every population must satisfy
+        |a - b| <= 50 steps x (8 x 2^-56 M + 16 x 2^-53 |b|),
+    and the worst relative error max |a - b| / |b| is reported."""
+    N, T = 64, 50
+    e, ux, uy, uz, n = I.periodic_box(N)
+    lat = _lattice((N, N, N), collision="mrt", tau_f=0.9, tau_v=0.9, tau_e=0.55, tau_eps=0.8)
+    lat.set_fields(e.cuda(), ux.cuda(), uy.cuda(), uz.cuda(), n.cuda())
+    lat.step(T)
+    a = lat.state("cpu").to(torch.float64)
+    lat.close()
+    prm = O.Params(collision="mrt", tau_f=0.9, tau_v=0.9, tau_e=0.55, tau_eps=0.8)
+    f, g = O.run(*O.init_populations(e, torch.stack([ux, uy, uz]), n), prm, T)
+    b = torch.cat([f, g])
+    d = (a - b).abs()
+    M = torch.cat([b[:19].abs().amax(0, keepdim=True).expand(19, -1, -1, -1),
+                   b[19:].abs().amax(0, keepdim=True).expand(19, -1, -1, -1)])
+    bound = T * (8 * 2.0 ** -56 * M + 16 * 2.0 ** -53 * b.abs())
+    ratio = float((d / bound).max())
+    rel = float((d / b.abs()).max())
+    units = float((d / (2.0 ** -56 * M)).max())
+    print("per-population: max |a-b|/|b| = %.3e, max |a-b| in node grid units = %.1f, max of |a-b|/bound = %.3f"
+          % (rel, units, ratio))
+    assert ratio <= 1.0, (ratio, rel, units)
