@@ -553,11 +553,13 @@ struct AdjPlan {
   int nsteps = -1, K = 0, nseg = 0, start_cur = 0, threads = 128, lanes = 128;
   bool quad = false;                          // reverse steps with four threads per node
   double wP = 0.0, wu = 0.0;                  // misfit weights baked into the graph
-  std::vector<void*> ckpt, seg, owned;
+  std::vector<void*> ckpt, seg, segb, owned;     // seg / segb: the recomputed states of alternate segments
   double *lam = nullptr, *mu = nullptr, *tb = nullptr, *lossn = nullptr, *sums = nullptr, *dde0 = nullptr;
   double* tgt = nullptr;
   void* g0copy = nullptr;
   cudaStream_t cap = nullptr;
+  cudaStream_t cap2 = nullptr;                // recompute of segment s - 1 beside the reverse sweep of s
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // fork, ready[2], free[2]
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
 };
@@ -568,6 +570,9 @@ void free_plan(void* p) {
   if (a->exec) cudaGraphExecDestroy(a->exec);
   if (a->graph) cudaGraphDestroy(a->graph);
   if (a->cap) cudaStreamDestroy(a->cap);
+  if (a->cap2) cudaStreamDestroy(a->cap2);
+  for (cudaEvent_t e : a->ev)
+    if (e) cudaEventDestroy(e);
   for (void* q : a->owned) cudaFree(q);
   delete a;
 }
@@ -609,25 +614,44 @@ cudaError_t enqueue_adjoint(rlb_handle* h, AdjPlan* a, double wP, double wu, boo
   k_adj_loss<<<grid, th, 0, st>>>(gT, tP, tP + N, tP + 2 * N, tP + 3 * N, wP, wu, a->lam, a->lossn, N);
   ENQ(cudaGetLastError());
   ENQ(cudaMemsetAsync(a->tb, 0, 3 * N * sizeof(double), st));
-  // reverse sweep, segment by segment, recomputing each from its checkpoint
+  // reverse sweep, segment by segment.  Each segment is recomputed from its checkpoint
+  // on the second stream into one of two state buffers (segment s into buffer s & 1),
+  // so the recompute of segment s - 1 runs beside the reverse sweep of segment s; a
+  // buffer is refilled only after the reverse sweep that read it.
+  cudaStream_t cs = a->cap2;
+  cudaEvent_t ev_fork = a->ev[0], ev_ready[2] = {a->ev[1], a->ev[2]}, ev_free[2] = {a->ev[3], a->ev[4]};
+  ENQ(cudaEventRecord(ev_fork, st));
+  ENQ(cudaStreamWaitEvent(cs, ev_fork, 0));
   void* saved[2] = {h->lat[0], h->lat[1]};
   const int saved_cur = h->cur;
-  for (int s = a->nseg - 1; s >= 0; --s) {
+  const std::vector<void*>* buf[2] = {&a->seg, &a->segb};
+  auto recompute = [&](int s) -> cudaError_t {
+    const std::vector<void*>& b = *buf[s & 1];
     const int t0 = s * K, t1 = std::min(T, t0 + K);
-    ENQ(cudaMemcpyAsync(a->seg[0], a->ckpt[s], state_bytes, cudaMemcpyDeviceToDevice, st));
-    for (int j = 0; j + 1 < t1 - t0; ++j) {   // seg[j] holds g^{t0 + j}
-      h->lat[0] = a->seg[j];
-      h->lat[1] = a->seg[j + 1];
+    cudaError_t r = cudaMemcpyAsync(b[0], a->ckpt[s], state_bytes, cudaMemcpyDeviceToDevice, cs);
+    for (int j = 0; r == cudaSuccess && j + 1 < t1 - t0; ++j) {   // b[j] holds g^{t0 + j}
+      h->lat[0] = b[j];
+      h->lat[1] = b[j + 1];
       h->cur = 0;
-      e = enqueue_steps(h, 1, st);
-      if (e != cudaSuccess) break;
+      r = enqueue_steps(h, 1, cs);
     }
     h->lat[0] = saved[0];
     h->lat[1] = saved[1];
     h->cur = saved_cur;
-    if (e != cudaSuccess) return e;
+    if (r == cudaSuccess) r = cudaEventRecord(ev_ready[s & 1], cs);
+    return r;
+  };
+  ENQ(recompute(a->nseg - 1));
+  for (int s = a->nseg - 1; s >= 0; --s) {
+    if (s >= 1) {
+      if (s + 1 <= a->nseg - 1) ENQ(cudaStreamWaitEvent(cs, ev_free[(s + 1) & 1], 0));
+      ENQ(recompute(s - 1));
+    }
+    ENQ(cudaStreamWaitEvent(st, ev_ready[s & 1], 0));
+    const std::vector<void*>& b = *buf[s & 1];
+    const int t0 = s * K, t1 = std::min(T, t0 + K);
     for (int t = t1 - 1; t >= t0; --t) {
-      const double* gt = (const double*)a->seg[t - t0] + 19 * N;
+      const double* gt = (const double*)b[t - t0] + 19 * N;
       // the last step reads lambda^T; later ones gather from the mu of the step after
       double* out = mu_cur == a->mu ? a->lam : a->mu;
       if (t == T - 1) {
@@ -648,7 +672,11 @@ cudaError_t enqueue_adjoint(rlb_handle* h, AdjPlan* a, double wP, double wu, boo
       }
       mu_cur = out;
     }
+    ENQ(cudaEventRecord(ev_free[s & 1], st));
   }
+  // join the second stream back into the capture
+  ENQ(cudaEventRecord(ev_fork, cs));
+  ENQ(cudaStreamWaitEvent(st, ev_fork, 0));
   ENQ(cudaGetLastError());
   k_adj_e0<<<grid3, th, 0, st>>>((const double*)a->g0copy + 19 * N, mu_cur, a->dde0, geo, lanes);
   k_rowsum<<<3, 256, 0, st>>>(a->tb, N, a->sums);
@@ -709,9 +737,13 @@ extern "C" int rlb_adjoint(rlb_handle* h, int nsteps, int checkpoint_every, cons
     a->quad = a->threads == 32;
     a->ckpt.assign(a->nseg, nullptr);
     a->seg.assign(a->K + 1, nullptr);
+    a->segb.assign(a->K + 1, nullptr);
     bool ok = true;
     for (int s = 0; s < a->nseg && ok; ++s) ok = plan_alloc(a, &a->ckpt[s], state_bytes);
     for (int j = 0; j <= a->K && ok; ++j) ok = plan_alloc(a, &a->seg[j], state_bytes);
+    for (int j = 0; j <= a->K && ok; ++j) ok = plan_alloc(a, &a->segb[j], state_bytes);
+    for (int i = 0; i < 5 && ok; ++i) ok = cudaEventCreateWithFlags(&a->ev[i], cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithFlags(&a->cap2, cudaStreamNonBlocking) == cudaSuccess;
     ok = ok && plan_alloc(a, (void**)&a->lam, gbytes) && plan_alloc(a, (void**)&a->mu, gbytes) &&
          plan_alloc(a, (void**)&a->tb, 3 * N * sizeof(double)) && plan_alloc(a, (void**)&a->lossn, N * sizeof(double)) &&
          plan_alloc(a, (void**)&a->sums, 8 * sizeof(double)) && plan_alloc(a, (void**)&a->dde0, N * sizeof(double)) &&
