@@ -1037,6 +1037,85 @@ __device__ __forceinline__ long long levels_to_int(const float (&v)[3], int E) {
   return LV > 2 ? k12 + level_int(v[2], E - 56) : k12;
 }
 
+// Two-level fast path of the exact sums, read back as integers on the FP32 pipe.  At
+// level L (grid unit u_L = 2^(E - 145 - 19 (L - 1))) every extracted part q is k u_L
+// with |k| <= 2^19, so a sum S of at most 8 parts is k u_L with |k| <= 2^22; then
+// S + C, C = 1.5 2^23 u_L, is exact and lies in C's binade or at its upper edge, where
+// the float bit patterns step by one per u_L: k = bits(S + C) - bits(C).  The sums are
+// taken in groups of at most 8 parts and the group integers added.  Returns the same
+// integers as levels_to_int<2> (unit 2^(E - 183)).  Needs 16 <= E <= 240 (normal C,
+// sigma) and every value within 2^13 of the largest (the third level is empty).
+#ifndef RLB_F32_GROUP_INT
+#define RLB_F32_GROUP_INT 1
+#endif
+__device__ __forceinline__ int group_int(float S, float C) {
+  return (int)(__float_as_uint(S + C) - __float_as_uint(C));
+}
+__device__ __forceinline__ void exact_ints_g2(const float (&g)[19], int E, long long& KT, long long& KX,
+                                              long long& KY, long long& KZ, float& Sa, float& Sd) {
+  const float sg[2] = {pow2_bits(E + 6), pow2_bits(E - 13)};
+  const float C[2] = {__uint_as_float(((unsigned)(E + 5) << 23) | 0x400000u),
+                      __uint_as_float(((unsigned)(E - 14) << 23) | 0x400000u)};
+  float r[19];
+#pragma unroll
+  for (int a = 0; a < 19; ++a) r[a] = g[a];
+  int kT[2], kX[2], kY[2], kZ[2];
+  Sa = 0.0f;
+  Sd = 0.0f;
+#pragma unroll
+  for (int L = 0; L < 2; ++L) {
+    float q[19];
+#pragma unroll
+    for (int a = 0; a < 19; ++a) {
+      const float t = sg[L] + r[a];
+      q[a] = t - sg[L];
+      r[a] = r[a] - q[a];
+    }
+    float sp[9], dp[9];
+#pragma unroll
+    for (int pp = 0; pp < 9; ++pp) {
+      sp[pp] = q[2 * pp + 1] + q[2 * pp + 2];
+      dp[pp] = q[2 * pp + 1] - q[2 * pp + 2];
+    }
+    const float sa = (sp[0] + sp[1]) + sp[2];
+    const float sd1 = (sp[3] + sp[4]) + sp[5], sd2 = (sp[6] + sp[7]) + sp[8];
+    Sa += sa;
+    Sd += sd1 + sd2;
+    kT[L] = group_int(q[0] + sa, C[L]) + group_int(sd1, C[L]) + group_int(sd2, C[L]);
+    kX[L] = group_int((dp[0] + dp[3]) + dp[4], C[L]) + group_int(dp[5] + dp[6], C[L]);
+    kY[L] = group_int((dp[1] + dp[3]) - dp[4], C[L]) + group_int(dp[7] + dp[8], C[L]);
+    kZ[L] = group_int((dp[2] + dp[5]) - dp[6], C[L]) + group_int(dp[7] - dp[8], C[L]);
+  }
+  KT = (((long long)kT[0] << 19) + kT[1]) << 19;
+  KX = (((long long)kX[0] << 19) + kX[1]) << 19;
+  KY = (((long long)kY[0] << 19) + kY[1]) << 19;
+  KZ = (((long long)kZ[0] << 19) + kZ[1]) << 19;
+}
+__device__ __forceinline__ long long exact_int_f2(const float (&f)[19], int E) {
+  const float sg[2] = {pow2_bits(E + 6), pow2_bits(E - 13)};
+  const float C[2] = {__uint_as_float(((unsigned)(E + 5) << 23) | 0x400000u),
+                      __uint_as_float(((unsigned)(E - 14) << 23) | 0x400000u)};
+  float r[19];
+#pragma unroll
+  for (int a = 0; a < 19; ++a) r[a] = f[a];
+  int k[2];
+#pragma unroll
+  for (int L = 0; L < 2; ++L) {
+    float q[19];
+#pragma unroll
+    for (int a = 0; a < 19; ++a) {
+      const float t = sg[L] + r[a];
+      q[a] = t - sg[L];
+      r[a] = r[a] - q[a];
+    }
+    const float s1 = ((q[0] + q[1]) + (q[2] + q[3])) + ((q[4] + q[5]) + q[6]);
+    const float s2 = ((q[7] + q[8]) + (q[9] + q[10])) + (q[11] + q[12]);
+    const float s3 = ((q[13] + q[14]) + (q[15] + q[16])) + (q[17] + q[18]);
+    k[L] = group_int(s1, C[L]) + group_int(s2, C[L]) + group_int(s3, C[L]);
+  }
+  return (((long long)k[0] << 19) + k[1]) << 19;
+}
+
 // FP32-storage node collide: the conserved sums exact (above) and delivered in
 // FP64, the recovery (sqrt, reciprocal) in FP64; equilibria, MRT projection and
 // relaxation in FP32 with one rounding on store.  Split into the g part (sums,
@@ -1057,7 +1136,13 @@ __device__ __forceinline__ void f32s_g_recover(const float (&g)[19], G32& s) {
   // recovery is homogeneous of degree 1 in (T00, M) (u is scale free), so it runs on
   // the unscaled K and scales after
   long long KT, KX, KY, KZ;
-  if (min_exp19(g) >= Eg - 13) {   // two extraction levels are exact
+  const bool two = min_exp19(g) >= Eg - 13;   // two extraction levels are exact
+  if (RLB_F32_GROUP_INT && two && Eg >= 16 && Eg <= 240) {
+    float sa, sd;
+    exact_ints_g2(g, Eg, KT, KX, KY, KZ, sa, sd);
+    S.Sa[0] = sa; S.Sa[1] = 0.0f; S.Sa[2] = 0.0f;
+    S.Sd[0] = sd; S.Sd[1] = 0.0f; S.Sd[2] = 0.0f;
+  } else if (two) {
     exact_sums_g<2>(g, Eg, S);
     KT = levels_to_int<2>(S.T00, Eg);
     KX = levels_to_int<2>(S.Mx, Eg);
@@ -1163,7 +1248,10 @@ __device__ __forceinline__ float f32s_f_sum(const float (&f)[19], bool& bad) {
   const int Ef = max_exp19(f);
   bad = Ef == 255;
   long long K;
-  if (min_exp19(f) >= Ef - 13) {   // two extraction levels are exact
+  const bool two = min_exp19(f) >= Ef - 13;   // two extraction levels are exact
+  if (RLB_F32_GROUP_INT && two && Ef >= 16 && Ef <= 240) {
+    K = exact_int_f2(f, Ef);
+  } else if (two) {
     exact_sum_f<2>(f, Ef, N0p);
     K = levels_to_int<2>(N0p, Ef);
   } else {
