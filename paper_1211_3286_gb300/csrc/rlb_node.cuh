@@ -235,6 +235,20 @@ __device__ __forceinline__ float d2f_rn_bits(double x) {
   return __uint_as_float(sign | mag);
 }
 
+// d2f_rn_bits(x * 2^es) for a normal or zero x: the power of two goes into the exponent
+// of the narrowed value (a zero x, exponent field 0, still flushes to zero).
+__device__ __forceinline__ float d2f_rn_bits_scaled(double x, int es) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned sign = hi & 0x80000000u;
+  const unsigned ex = (hi >> 20) & 0x7ffu;
+  const int e = (int)ex + es - 896;
+  unsigned mag = ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const unsigned tail = lo & 0x1fffffffu;
+  mag += (tail > 0x10000000u) | ((tail == 0x10000000u) & (mag & 1u));
+  mag = (ex == 0u || e < 1) ? 0u : (e > 254 ? 0x7f800000u : mag);
+  return __uint_as_float(sign | mag);
+}
+
 // Integer sign / magnitude tests on the high word of a double.
 __device__ __forceinline__ bool pos_finite_hi(double x) {   // x > 0, finite (hi word of a normal positive)
   const int hi = __double2hiint(x);
@@ -1169,23 +1183,23 @@ __device__ __forceinline__ void f32s_g_recover(const float (&g)[19], G32& s) {
   // sigma u^2 = |M|^2 / sigma
   const double su2u = MM * is;
   const double P3u = 3.0 * Pu;
-  s.su2 = d2f_rn_bits(scale_pow2(su2u, eg));
-  s.kg = d2f_rn_bits(scale_pow2(fma(-1.5, su2u, P3u), eg));
-  s.geq0 = d2f_rn_bits(scale_pow2(fma(-0.5, su2u, sgu - P3u), eg));
+  s.su2 = d2f_rn_bits_scaled(su2u, eg);
+  s.kg = d2f_rn_bits_scaled(fma(-1.5, su2u, P3u), eg);
+  s.geq0 = d2f_rn_bits_scaled(fma(-0.5, su2u, sgu - P3u), eg);
   s.ux = d2f_rn_bits(Mxu * is);
   s.uy = d2f_rn_bits(Myu * is);
   s.uz = d2f_rn_bits(Mzu * is);
-  s.sg = d2f_rn_bits(scale_pow2(sgu, eg));
-  s.P = d2f_rn_bits(scale_pow2(Pu, eg));
+  s.sg = d2f_rn_bits_scaled(sgu, eg);
+  s.P = d2f_rn_bits_scaled(Pu, eg);
   if (MRT) {
     // non-equilibrium class sums in FP32 (their rounding is far below the FP32 storage rounding)
     s.Sa = (S.Sa[0] + S.Sa[1]) + S.Sa[2];
     s.Sd = (S.Sd[0] + S.Sd[1]) + S.Sd[2];
   }
   if (QSEP) {
-    s.Mx = d2f_rn_bits(scale_pow2(Mxu, eg));
-    s.My = d2f_rn_bits(scale_pow2(Myu, eg));
-    s.Mz = d2f_rn_bits(scale_pow2(Mzu, eg));
+    s.Mx = d2f_rn_bits_scaled(Mxu, eg);
+    s.My = d2f_rn_bits_scaled(Myu, eg);
+    s.Mz = d2f_rn_bits_scaled(Mzu, eg);
   }
   const float u2 = fmaf(s.ux, s.ux, fmaf(s.uy, s.uy, s.uz * s.uz));
   // A > 0, T00 > 0, P > 0 (all finite), u^2 < 1 (on the rounded velocity; NaN fails)
@@ -1258,7 +1272,7 @@ __device__ __forceinline__ float f32s_f_sum(const float (&f)[19], bool& bad) {
     exact_sum_f<3>(f, Ef, N0p);
     K = levels_to_int<3>(N0p, Ef);
   }
-  return d2f_rn_bits(scale_pow2(fx::from_fixed_int(K, 1079), Ef - 183));
+  return d2f_rn_bits_scaled(fx::from_fixed_int(K, 1079), Ef - 183);
 }
 
 __device__ __forceinline__ void f32s_f_relax(float (&f)[19], float N0, float ux, float uy, float uz,
