@@ -175,6 +175,7 @@ __global__ void __launch_bounds__(sizeof(S) == 8 ? 256 : RLB_TUBES_F32_THREADS, 
                         unsigned long long* __restrict__ bad) {
   __shared__ int s_t;
   __shared__ S edge[2][2][5];   // [left/right end][f/g][link with c_x = +1 / its opposite]
+  __shared__ StepConst s_k;     // the tube's constants, read from shared memory where used
   for (;;) {
     if (threadIdx.x == 0) s_t = (int)atomicAdd(counter, 1u);
     __syncthreads();
@@ -182,7 +183,8 @@ __global__ void __launch_bounds__(sizeof(S) == 8 ? 256 : RLB_TUBES_F32_THREADS, 
     __syncthreads();
     if (t >= ntubes) return;
     const TubeInfo ti = order[t];
-    const StepConst k = consts[ti.id];
+    if (threadIdx.x == 0) s_k = consts[ti.id];
+    const StepConst& k = s_k;
     // edge copies of layout N: the end nodes' own populations of the clamped links
     if (threadIdx.x < 20) {
       const int side = threadIdx.x / 10, d = (threadIdx.x / 5) & 1, j = threadIdx.x % 5;
