@@ -219,6 +219,20 @@ __device__ __forceinline__ void g_collide_vjp(const double (&h)[19], const doubl
 // the nodes whose pull of link a lands on (x, y, z) (at most two per axis: the
 // neighbour, and at a zero-gradient end the node itself).  Loads are unrolled and
 // predicated; the order of the sum is fixed.
+// The same on a quasi-1D lattice (ny = nz = 1), where every pull's y and z source and
+// preimage is the node's own row: only the x preimages are summed, in the same order.
+__device__ __forceinline__ double gather_link_tube(const double* __restrict__ mu_a, int x, int cx, const AGeo& geo) {
+  int px[2];
+  const int nxp = preimages(x, cx, geo.nx, geo.zgx, px);
+  double acc = 0.0;
+#pragma unroll
+  for (int ix = 0; ix < 2; ++ix)
+    if (ix < nxp) acc += mu_a[px[ix]];
+  return acc;
+}
+template <bool TUBE>
+__device__ __forceinline__ double gather_any(const double* __restrict__ mu_a, int x, int y, int z, int cx, int cy,
+                                             int cz, const AGeo& geo);
 __device__ __forceinline__ double gather_link(const double* __restrict__ mu_a, int x, int y, int z, int cx, int cy,
                                               int cz, const AGeo& geo) {
   int px[2], py[2], pz[2];
@@ -236,11 +250,18 @@ __device__ __forceinline__ double gather_link(const double* __restrict__ mu_a, i
           acc += mu_a[((unsigned long long)pz[iz] * geo.ny + py[iy]) * geo.nx + px[ix]];
   return acc;
 }
+template <bool TUBE>
+__device__ __forceinline__ double gather_any(const double* __restrict__ mu_a, int x, int y, int z, int cx, int cy,
+                                             int cz, const AGeo& geo) {
+  if constexpr (TUBE) return gather_link_tube(mu_a, x, cx, geo);
+  else return gather_link(mu_a, x, y, z, cx, cy, cz, geo);
+}
 
 // One reverse step at node (x, y, z) of a (ceil(nx / blockDim), ny, nz) grid: lambda^{t+1}
 // at the node (read directly for the last step, FIRST, else gathered from the mu of the
 // step after it), then mu = C_h^T lambda^{t+1} and the omega contributions.
-template <bool MRT, bool FIRST>
+// TUBE: ny = nz = 1 (only x-neighbours exchange populations).
+template <bool MRT, bool FIRST, bool TUBE = false>
 __global__ void __launch_bounds__(kThreads) k_adj_step(const double* __restrict__ g, const double* __restrict__ in,
                                                       double* __restrict__ mu, double* __restrict__ tb, AGeo geo,
                                                       StepConst k, int lanes) {
@@ -253,12 +274,13 @@ __global__ void __launch_bounds__(kThreads) k_adj_step(const double* __restrict_
 #pragma unroll
   for (int a = 0; a < 19; ++a) {
     const int xs = pull_src(x, link_cx(a), geo.nx, geo.zgx);
-    const int ys = pull_src(y, link_cy(a), geo.ny, geo.zgy);
-    const int zs = pull_src(z, link_cz(a), geo.nz, geo.zgz);
+    const int ys = TUBE ? 0 : pull_src(y, link_cy(a), geo.ny, geo.zgy);
+    const int zs = TUBE ? 0 : pull_src(z, link_cz(a), geo.nz, geo.zgz);
     const unsigned long long s = ((unsigned long long)zs * geo.ny + ys) * geo.nx + xs;
     h[a] = g[(unsigned long long)a * geo.n + s];
     lo[a] = FIRST ? in[(unsigned long long)a * geo.n + i]
-                  : gather_link(in + (unsigned long long)a * geo.n, x, y, z, link_cx(a), link_cy(a), link_cz(a), geo);
+                  : gather_any<TUBE>(in + (unsigned long long)a * geo.n, x, y, z, link_cx(a), link_cy(a), link_cz(a),
+                                     geo);
   }
   double wvb, web, wpb;
   g_collide_vjp<MRT>(h, lo, k, hb, wvb, web, wpb);
@@ -300,7 +322,7 @@ __device__ __forceinline__ double quad_sum(double v) {
 }
 
 // One reverse step on a (ceil(4 nx / blockDim), ny, nz) grid, blockDim a multiple of 32.
-template <bool MRT, bool FIRST>
+template <bool MRT, bool FIRST, bool TUBE = false>
 __global__ void __launch_bounds__(kThreads) k_adj_step_quad(const double* __restrict__ g,
                                                            const double* __restrict__ in, double* __restrict__ mu,
                                                            double* __restrict__ tb, AGeo geo, StepConst k) {
@@ -326,14 +348,18 @@ __global__ void __launch_bounds__(kThreads) k_adj_step_quad(const double* __rest
     ha[s] = hb[s] = la[s] = lb[s] = 0.0;
     if (p <= 8) {
       const unsigned long long a1 = 2 * p + 1, a2 = 2 * p + 2;
-      const unsigned long long s1 = ((unsigned long long)pull_src(z, cz, geo.nz, geo.zgz) * geo.ny +
-                                     pull_src(y, cy, geo.ny, geo.zgy)) * geo.nx + pull_src(x, cx, geo.nx, geo.zgx);
-      const unsigned long long s2 = ((unsigned long long)pull_src(z, -cz, geo.nz, geo.zgz) * geo.ny +
-                                     pull_src(y, -cy, geo.ny, geo.zgy)) * geo.nx + pull_src(x, -cx, geo.nx, geo.zgx);
+      const unsigned long long s1 =
+          TUBE ? (unsigned long long)pull_src(x, cx, geo.nx, geo.zgx)
+               : ((unsigned long long)pull_src(z, cz, geo.nz, geo.zgz) * geo.ny + pull_src(y, cy, geo.ny, geo.zgy)) *
+                         geo.nx + pull_src(x, cx, geo.nx, geo.zgx);
+      const unsigned long long s2 =
+          TUBE ? (unsigned long long)pull_src(x, -cx, geo.nx, geo.zgx)
+               : ((unsigned long long)pull_src(z, -cz, geo.nz, geo.zgz) * geo.ny + pull_src(y, -cy, geo.ny, geo.zgy)) *
+                         geo.nx + pull_src(x, -cx, geo.nx, geo.zgx);
       ha[s] = g[a1 * n + s1];
       hb[s] = g[a2 * n + s2];
-      la[s] = FIRST ? in[a1 * n + i] : gather_link(in + a1 * n, x, y, z, cx, cy, cz, geo);
-      lb[s] = FIRST ? in[a2 * n + i] : gather_link(in + a2 * n, x, y, z, -cx, -cy, -cz, geo);
+      la[s] = FIRST ? in[a1 * n + i] : gather_any<TUBE>(in + a1 * n, x, y, z, cx, cy, cz, geo);
+      lb[s] = FIRST ? in[a2 * n + i] : gather_any<TUBE>(in + a2 * n, x, y, z, -cx, -cy, -cz, geo);
     }
   }
   // ---- forward intermediates: moments over the four lanes, then the scalar chain
@@ -587,6 +613,30 @@ bool plan_alloc(AdjPlan* a, void** p, size_t bytes) {
   return true;
 }
 
+// One reverse step with the kernel variant for the lattice: four threads per node or
+// one, quasi-1D (ny = nz = 1) or general, BGK or MRT.
+template <bool FIRST>
+cudaError_t reverse_step(bool quad, bool tube, bool mrt, dim3 grid4, dim3 grid3, int th, cudaStream_t st,
+                         const double* gt, const double* in, double* out, double* tb, const AGeo& geo,
+                         const StepConst& k, int lanes) {
+  if (quad) {
+    if (tube) {
+      if (mrt) k_adj_step_quad<true, FIRST, true><<<grid4, th, 0, st>>>(gt, in, out, tb, geo, k);
+      else k_adj_step_quad<false, FIRST, true><<<grid4, th, 0, st>>>(gt, in, out, tb, geo, k);
+    } else {
+      if (mrt) k_adj_step_quad<true, FIRST><<<grid4, th, 0, st>>>(gt, in, out, tb, geo, k);
+      else k_adj_step_quad<false, FIRST><<<grid4, th, 0, st>>>(gt, in, out, tb, geo, k);
+    }
+  } else if (tube) {
+    if (mrt) k_adj_step<true, FIRST, true><<<grid3, th, 0, st>>>(gt, in, out, tb, geo, k, lanes);
+    else k_adj_step<false, FIRST, true><<<grid3, th, 0, st>>>(gt, in, out, tb, geo, k, lanes);
+  } else {
+    if (mrt) k_adj_step<true, FIRST><<<grid3, th, 0, st>>>(gt, in, out, tb, geo, k, lanes);
+    else k_adj_step<false, FIRST><<<grid3, th, 0, st>>>(gt, in, out, tb, geo, k, lanes);
+  }
+  return cudaGetLastError();
+}
+
 // Enqueue the whole gradient computation on stream st (captured into the plan's graph).
 cudaError_t enqueue_adjoint(rlb_handle* h, AdjPlan* a, double wP, double wu, bool mrt) {
   const unsigned long long N = h->nodes;
@@ -600,6 +650,7 @@ cudaError_t enqueue_adjoint(rlb_handle* h, AdjPlan* a, double wP, double wu, boo
   cudaStream_t st = a->cap;
   AGeo geo{h->cfg.nx, h->cfg.ny, h->cfg.nz, h->cfg.bc[0] == RLB_ZERO_GRADIENT, h->cfg.bc[1] == RLB_ZERO_GRADIENT,
            h->cfg.bc[2] == RLB_ZERO_GRADIENT, N};
+  const bool tube = h->cfg.ny == 1 && h->cfg.nz == 1;
   const double* tP = a->tgt;
   cudaError_t e;
 #define ENQ(call) do { e = (call); if (e != cudaSuccess) return e; } while (0)
@@ -656,19 +707,9 @@ cudaError_t enqueue_adjoint(rlb_handle* h, AdjPlan* a, double wP, double wu, boo
       double* out = mu_cur == a->mu ? a->lam : a->mu;
       if (t == T - 1) {
         out = a->mu;
-        if (a->quad) {
-          if (mrt) k_adj_step_quad<true, true><<<grid4, th, 0, st>>>(gt, a->lam, out, a->tb, geo, h->k);
-          else k_adj_step_quad<false, true><<<grid4, th, 0, st>>>(gt, a->lam, out, a->tb, geo, h->k);
-        } else {
-          if (mrt) k_adj_step<true, true><<<grid3, th, 0, st>>>(gt, a->lam, out, a->tb, geo, h->k, lanes);
-          else k_adj_step<false, true><<<grid3, th, 0, st>>>(gt, a->lam, out, a->tb, geo, h->k, lanes);
-        }
-      } else if (a->quad) {
-        if (mrt) k_adj_step_quad<true, false><<<grid4, th, 0, st>>>(gt, mu_cur, out, a->tb, geo, h->k);
-        else k_adj_step_quad<false, false><<<grid4, th, 0, st>>>(gt, mu_cur, out, a->tb, geo, h->k);
+        ENQ(reverse_step<true>(a->quad, tube, mrt, grid4, grid3, th, st, gt, a->lam, out, a->tb, geo, h->k, lanes));
       } else {
-        if (mrt) k_adj_step<true, false><<<grid3, th, 0, st>>>(gt, mu_cur, out, a->tb, geo, h->k, lanes);
-        else k_adj_step<false, false><<<grid3, th, 0, st>>>(gt, mu_cur, out, a->tb, geo, h->k, lanes);
+        ENQ(reverse_step<false>(a->quad, tube, mrt, grid4, grid3, th, st, gt, mu_cur, out, a->tb, geo, h->k, lanes));
       }
       mu_cur = out;
     }

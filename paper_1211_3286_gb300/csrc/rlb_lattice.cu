@@ -318,6 +318,205 @@ __global__ void __launch_bounds__(64 * W, W == 1 ? 14 : RLB_WS_WARPS_PER_SM / (2
   }
 }
 
+// FP64 step for small lattices with four lanes per node and distribution: a 64-thread
+// block serves 8 nodes along x, warp 0 their g and warp 1 their f.  Lane j = 0, 1, 2 of
+// a node holds axis pair j (links 2j + 1, 2j + 2) and the two diagonal pairs of one
+// plane, (a, b) = (x, y), (y, z), (x, z): the pairs e_a + e_b and e_a - e_b (pairs 3-4,
+// 7-8, 5-6), six links each; lane 3 holds the rest link.  The block exponent, the exact
+// integer sums and the rest value are combined over the node's lanes with shuffles, the
+// recovery and the equilibrium pieces run in every lane, and each lane relaxes and
+// stores its own links: the arithmetic of k_step_ws, link for link, with a node's
+// dependent chain about a third as long.  u goes to the f warp through shared memory
+// across named barrier 1.  No separate tau_q (QSEP) in this form.
+__device__ __forceinline__ long long quad_sum64(long long v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  return v;
+}
+__device__ __forceinline__ long long sel3(int j, long long v0, long long v1, long long v2) {
+  return j == 0 ? v0 : (j == 1 ? v1 : v2);
+}
+
+template <bool MRT>
+__global__ void __launch_bounds__(64, 8) k_step_quad(const double* __restrict__ src, double* __restrict__ dst, Geo geo,
+                                                     StepConst k, unsigned long long* __restrict__ bad) {
+  using namespace fx;
+  __shared__ unsigned long long s_ax[8], s_ay[8], s_az[8];
+  __shared__ unsigned s_sg[8];
+  const int lane = threadIdx.x & 31;
+  const bool is_g = threadIdx.x < 32;
+  const int m = lane >> 2, j = lane & 3;
+  const int xv = blockIdx.x * 8 + m;
+  const bool valid = xv < geo.nx;
+  const int x = valid ? xv : geo.nx - 1;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const int xm = src_minus(x, geo.nx, geo.bcx), xp = src_plus(x, geo.nx, geo.bcx);
+  const int ym = src_minus(y, geo.ny, geo.bcy), yp = src_plus(y, geo.ny, geo.bcy);
+  const int zm = src_minus(z, geo.nz, geo.bcz), zp = src_plus(z, geo.nz, geo.bcz);
+  // this lane's axes: axis pair i = j; diagonal plane (a, b) = (x, y), (y, z), (x, z)
+  const int ai = j < 3 ? j : 0, da = j == 1 ? 1 : 0, db = j == 0 ? 1 : 2;
+  const int pd = j == 0 ? 3 : (j == 1 ? 7 : 5);   // first diagonal pair of the plane
+  // slot sl: link and direction (slots 0-1 the axis pair, 2-3 pair pd, 4-5 pair pd + 1);
+  // lane 3 reads the rest link in every slot
+  int link[6], cxs[6], cys[6], czs[6];
+#pragma unroll
+  for (int sl = 0; sl < 6; ++sl) {
+    int cx, cy, cz;
+    if (sl < 2) {
+      const int c = sl == 0 ? 1 : -1;
+      cx = ai == 0 ? c : 0;
+      cy = ai == 1 ? c : 0;
+      cz = ai == 2 ? c : 0;
+      link[sl] = 2 * ai + 1 + sl;
+    } else {
+      const int sa = (sl & 1) ? -1 : 1;              // +(e_a + e_b), -(e_a + e_b), +(e_a - e_b), -(e_a - e_b)
+      const int sb = sl < 4 ? sa : -sa;
+      cx = da == 0 ? sa : 0;                          // db is never x
+      cy = (da == 1 ? sa : 0) + (db == 1 ? sb : 0);
+      cz = db == 2 ? sb : 0;                          // da is never z
+      link[sl] = 2 * pd + 1 + (sl - 2);
+    }
+    const bool rest = j == 3;
+    link[sl] = rest ? 0 : link[sl];
+    cxs[sl] = rest ? 0 : cx;
+    cys[sl] = rest ? 0 : cy;
+    czs[sl] = rest ? 0 : cz;
+  }
+  const unsigned long long plane0 = is_g ? 19ull * geo.plane : 0ull;
+  double v[6];
+#pragma unroll
+  for (int sl = 0; sl < 6; ++sl) {
+    const int sx = cxs[sl] > 0 ? xm : (cxs[sl] < 0 ? xp : x);
+    const int sy = cys[sl] > 0 ? ym : (cys[sl] < 0 ? yp : y);
+    const int sz = czs[sl] > 0 ? zm : (czs[sl] < 0 ? zp : z);
+    const unsigned idx = ((unsigned)sz * (unsigned)geo.ny + (unsigned)sy) * (unsigned)geo.nx + (unsigned)sx;
+    v[sl] = ldg_nc(src + plane0 + (unsigned long long)link[sl] * geo.plane + idx);
+  }
+  // block exponent over the node's 19 values (max over its four lanes)
+  int hmax = __double2hiint(v[0]), hmin = hmax;
+#pragma unroll
+  for (int sl = 1; sl < 6; ++sl) {
+    const int h = __double2hiint(v[sl]);
+    hmax = max(hmax, h);
+    hmin = min(hmin, h);
+  }
+  hmax = max(hmax, __shfl_xor_sync(0xffffffffu, hmax, 1));
+  hmax = max(hmax, __shfl_xor_sync(0xffffffffu, hmax, 2));
+  const bool fast = __all_sync(0xffffffffu, hmin > 0 && hmax < 0x7ff00000 && hmin >= (((hmax >> 20) - 24) << 20));
+  int E;
+  long long X[6];
+  if (fast) {
+    E = hmax >> 20;
+#pragma unroll
+    for (int sl = 0; sl < 6; ++sl) X[sl] = to_fixed_pos(v[sl], E + 7);
+  } else {
+    unsigned me = 0;
+#pragma unroll
+    for (int sl = 0; sl < 6; ++sl) me = max(me, (unsigned)__double2hiint(v[sl]) & 0x7ff00000u);
+    me = max(me, (unsigned)__shfl_xor_sync(0xffffffffu, (int)me, 1));
+    me = max(me, (unsigned)__shfl_xor_sync(0xffffffffu, (int)me, 2));
+    E = (int)(me >> 20);
+#pragma unroll
+    for (int sl = 0; sl < 6; ++sl) X[sl] = to_fixed(v[sl], E + 7);
+  }
+  const int base = lane & ~3;
+  const long long Xr = __shfl_sync(0xffffffffu, X[0], base + 3);   // the rest link's value
+  const long long spa = X[0] + X[1], dpa = X[0] - X[1];
+  const long long spp = X[2] + X[3], dpp = X[2] - X[3];
+  const long long spm = X[4] + X[5], dpm = X[4] - X[5];
+  const bool pairs = j < 3;
+  UFix u;
+  unsigned long long sig = 0;
+  long long Pf = 0, Sa = 0, Sd = 0, N0 = 0;
+  bool b = (E < 64) | (E > 2046);
+  if (is_g) {
+    Sa = quad_sum64(pairs ? spa : 0);
+    Sd = quad_sum64(pairs ? spp + spm : 0);
+    const long long T00 = Xr + Sa + Sd;
+    // momentum: lane 0 adds dp(x) + pairs 3, 4 to M_x and 3 - 4 to M_y; lane 1 dp(y) +
+    // pairs 7, 8 to M_y and 7 - 8 to M_z; lane 2 dp(z) and 5 - 6 to M_z, 5 + 6 to M_x
+    const long long S2 = dpp + dpm, S3 = dpp - dpm;
+    const long long Mx = quad_sum64(j == 0 ? dpa + S2 : (j == 2 ? S2 : 0));
+    const long long My = quad_sum64(j == 0 ? S3 : (j == 1 ? dpa + S2 : 0));
+    const long long Mz = quad_sum64(j == 1 ? S3 : (j == 2 ? dpa + S3 : 0));
+    bool br;
+    sig = fx_recover(T00, Mx, My, Mz, u, br);
+    Pf = (long long)sig - T00;
+    if (j == 0) {
+      s_ax[m] = u.ax;
+      s_ay[m] = u.ay;
+      s_az[m] = u.az;
+      s_sg[m] = u.sx | (u.sy << 1) | (u.sz << 2);
+    }
+    ufix_products(u);
+    b |= br | (Pf <= 0) | (u.xx + u.yy + u.zz >= (1ull << 62));
+  } else {
+    N0 = Xr + quad_sum64(pairs ? (spa + spp) + spm : 0);
+  }
+  asm volatile("bar.sync 1, 64;" ::: "memory");
+  if (!is_g) {
+    u.ax = s_ax[m];
+    u.ay = s_ay[m];
+    u.az = s_az[m];
+    const unsigned sg = s_sg[m];
+    u.sx = sg & 1u;
+    u.sy = (sg >> 1) & 1u;
+    u.sz = sg >> 2;
+    ufix_products(u);
+  }
+  EqPieces q;
+  eq_pieces(is_g ? sig : (unsigned long long)N0, u, q);
+  const long long SX = q.Xx + q.Xy + q.Xz;
+  long long eq0;
+  if (is_g) {
+    q.KA = (long long)mulhi((unsigned long long)Pf, kSixth) - (long long)mulhi((unsigned long long)SX, kThird);
+    eq0 = (long long)sig - 3 * Pf - 2 * SX;
+  } else {
+    q.KA = (long long)mulhi((unsigned long long)N0, kEighteenth) - (long long)mulhi((unsigned long long)SX, kThird);
+    eq0 = (long long)mulhi((unsigned long long)N0, kThird) - 2 * SX;
+  }
+  const unsigned long long Om = is_g ? k.Om_v : k.Om_f;
+  long long c0 = (long long)(Om >> 1), cA = c0, cD = c0;
+  if (MRT && is_g) {
+    const long long n0 = (Xr - eq0) >> 3;
+    const long long nA = (Sa - Pf) >> 3;
+    const long long nD = (Sd - Pf - 2 * SX) >> 3;
+    const long long ae = __mul64hi(8 * nD - 11 * nA - 30 * n0, k.CE) >> 6;
+    const long long ap = __mul64hi(nD - 4 * nA + 12 * n0, k.CP) >> 2;
+    c0 += 30 * ae - 12 * ap;
+    cA += 11 * ae + 4 * ap;
+    cD -= 8 * ae + ap;
+  }
+  const unsigned node = ((unsigned)z * (unsigned)geo.ny + (unsigned)y) * (unsigned)geo.nx + (unsigned)x;
+  if (valid && b && j == 0) atomicMin(bad, (unsigned long long)node);
+  double* out = dst + plane0 + node;
+  if (pairs) {
+    // axis pair: ev = KA + X_i, od = Z_i; diagonal pairs: ev = KA/2 + (X_a + X_b)/2 +- Y_ab,
+    // od = (Z_a +- Z_b)/2 (the pieces of relax_links_store)
+    const long long Xi = sel3(ai, q.Xx, q.Xy, q.Xz), Zi = sel3(ai, q.Zx, q.Zy, q.Zz);
+    const long long Xa = sel3(da, q.Xx, q.Xy, q.Xz), Xb = sel3(db, q.Xx, q.Xy, q.Xz);
+    const long long Za = sel3(da, q.Zx, q.Zy, q.Zz), Zb = sel3(db, q.Zx, q.Zy, q.Zz);
+    const long long Yab = j == 0 ? q.Yxy : (j == 1 ? q.Yyz : q.Yxz);
+    const long long evA = q.KA + Xi, odA = Zi;
+    const long long evD = (q.KA >> 1) + ((Xa + Xb) >> 1);
+    const long long evP = evD + Yab, odP = (Za + Zb) >> 1;
+    const long long evM = evD - Yab, odM = (Za - Zb) >> 1;
+    const long long y0 = relax(X[0], evA + odA, Om, cA), y1 = relax(X[1], evA - odA, Om, cA);
+    const long long y2 = relax(X[2], evP + odP, Om, cD), y3 = relax(X[3], evP - odP, Om, cD);
+    const long long y4 = relax(X[4], evM + odM, Om, cD), y5 = relax(X[5], evM - odM, Om, cD);
+    if (valid) {
+      out[(unsigned long long)link[0] * geo.plane] = from_fixed_dp(y0, E);
+      out[(unsigned long long)link[1] * geo.plane] = from_fixed_dp(y1, E);
+      out[(unsigned long long)link[2] * geo.plane] = from_fixed_dp(y2, E);
+      out[(unsigned long long)link[3] * geo.plane] = from_fixed_dp(y3, E);
+      out[(unsigned long long)link[4] * geo.plane] = from_fixed_dp(y4, E);
+      out[(unsigned long long)link[5] * geo.plane] = from_fixed_dp(y5, E);
+    }
+  } else if (valid) {
+    out[0] = from_fixed_dp(relax(X[0], eq0, Om, c0), E);
+  }
+}
+
 // D2Q9 pull of the 9 f and 9 g arriving at node (x, y).
 __device__ __forceinline__ unsigned pull_d2q9(const double* __restrict__ src, const Geo& geo, int x, int y,
                                               double (&f)[9], double (&g)[9]) {
@@ -511,11 +710,14 @@ cudaError_t launch_step(rlb_handle* h, const void* src, void* dst, cudaStream_t 
     // warp roles: 64-thread blocks (one g and one f warp) for small lattices
     const double* s8 = (const double*)src;
     double* d8 = (double*)dst;
-    if (bx == 32) {
+    if (bx == 32 && !q) {
+      // four lanes per node: 8 nodes per 64-thread block
+      dim3 gq((geo.nx + 7) / 8, geo.ny, geo.nz);
+      if (!mrt) k_step_quad<false><<<gq, 64, 0, st>>>(s8, d8, geo, h->k, h->d_bad);
+      else k_step_quad<true><<<gq, 64, 0, st>>>(s8, d8, geo, h->k, h->d_bad);
+    } else if (bx == 32) {
       dim3 gw((geo.nx + 31) / 32, geo.ny, geo.nz);
-      if (!mrt) k_step_ws<1, false, false><<<gw, 64, 0, st>>>(s8, d8, geo, h->k, h->d_bad);
-      else if (!q) k_step_ws<1, true, false><<<gw, 64, 0, st>>>(s8, d8, geo, h->k, h->d_bad);
-      else k_step_ws<1, true, true><<<gw, 64, 0, st>>>(s8, d8, geo, h->k, h->d_bad);
+      k_step_ws<1, true, true><<<gw, 64, 0, st>>>(s8, d8, geo, h->k, h->d_bad);
     } else {
       constexpr int W = RLB_WS_WARPS;
       dim3 gw((geo.nx + 32 * W - 1) / (32 * W), geo.ny, geo.nz);

@@ -465,3 +465,37 @@ def test_fp64_step_per_population_precision_64_cubed():
     print("per-population: max |a-b|/|b| = %.3e, max |a-b| in node grid units = %.1f, max of |a-b|/bound = %.3f"
           % (rel, units, ratio))
     assert ratio <= 1.0, (ratio, rel, units)
+
+
+# ----------------------------------------------------------------------------- small-lattice kernel
+@pytest.mark.parametrize("shape, reps, collision, bc, umax", [
+    ((5, 7, 301), 4, "mrt", ("periodic",) * 3, 0.3),                                 # ragged nx = 37 x 8 + 5
+    ((3, 5, 205), 13, "bgk", ("zero_gradient", "zero_gradient", "periodic"), 0.3),
+    ((2, 9, 131), 17, "mrt", ("zero_gradient", "periodic", "periodic"), 0.85),       # negative rest links
+    ((1, 1, 1600), 25, "mrt", ("zero_gradient", "periodic", "periodic"), None),      # the adjoint's tube
+])
+def test_small_lattice_step_bitwise_equals_wide_step(shape, reps, collision, bc, umax):
+    """Lattices of at most 38,912 nodes take the FP64 step with four lanes per node; larger
+    ones take the 128-node blocks.  Both do the same integer arithmetic per link, so a
+    lattice and its copy tiled `reps` times along a periodic z axis (above the threshold)
+    must hold bit-identical populations after every step."""
+    nz, ny, nx = shape
+    assert nz * ny * nx <= 38912 < reps * nz * ny * nx
+    if umax is None:
+        e, ux, uy, uz, n = _tube(nx)
+        e, ux, uy, uz, n = (t.reshape(shape) for t in (e, ux, uy, uz, n))
+    else:
+        e, ux, uy, uz, n = I.periodic_box(None, seed=31, shape=shape, umax=umax)
+    kw = dict(collision=collision, tau_f=0.7, tau_v=0.9, tau_e=0.55, tau_eps=0.8, bc=bc)
+    small = _lattice(shape, **kw)
+    big = _lattice((reps * nz, ny, nx), **kw)
+    small.set_fields(*(t.cuda() for t in (e, ux, uy, uz, n)))
+    big.set_fields(*(t.repeat(reps, 1, 1).cuda() for t in (e, ux, uy, uz, n)))
+    for steps in (1, 1, 20):
+        small.step(steps)
+        big.step(steps)
+        a = small.state().view(torch.int64)
+        b = big.state().view(torch.int64).reshape(-1, reps, nz, ny, nx)
+        assert torch.equal(b, a.unsqueeze(1).expand_as(b)), steps
+    small.close()
+    big.close()
