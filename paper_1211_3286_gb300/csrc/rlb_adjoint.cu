@@ -321,22 +321,12 @@ __device__ __forceinline__ double quad_sum(double v) {
   return v;
 }
 
-// One reverse step on a (ceil(4 nx / blockDim), ny, nz) grid, blockDim a multiple of 32.
-template <bool MRT, bool FIRST, bool TUBE = false>
-__global__ void __launch_bounds__(kThreads) k_adj_step_quad(const double* __restrict__ g,
-                                                           const double* __restrict__ in, double* __restrict__ mu,
-                                                           double* __restrict__ tb, AGeo geo, StepConst k) {
-  const int j = threadIdx.x & 3;
-  const int xg = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 2);
-  const bool valid = xg < geo.nx;
-  const int x = valid ? xg : geo.nx - 1;   // lanes past the row repeat its last node and store nothing
-  const int y = blockIdx.y, z = blockIdx.z;
+// The pulled g of lane j's three link pairs p = j, j + 4, j + 8 at node (x, y, z) (zeros
+// for p > 8) and their directions.
+template <bool TUBE>
+__device__ __forceinline__ void quad_pull(const double* __restrict__ g, int x, int y, int z, int j, const AGeo& geo,
+                                          double (&ha)[3], double (&hb)[3], int (&cd)[3][3]) {
   const unsigned long long n = geo.n;
-  const unsigned long long i = ((unsigned long long)z * geo.ny + y) * geo.nx + x;
-  const double h0 = g[i];
-  const double l0 = in[i];   // the rest link's lambda is mu at the node itself
-  double ha[3], hb[3], la[3], lb[3];
-  int cd[3][3];
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
     const int p = j + 4 * s;
@@ -345,7 +335,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_step_quad(const double* __rest
     cd[s][0] = cx;
     cd[s][1] = cy;
     cd[s][2] = cz;
-    ha[s] = hb[s] = la[s] = lb[s] = 0.0;
+    ha[s] = hb[s] = 0.0;
     if (p <= 8) {
       const unsigned long long a1 = 2 * p + 1, a2 = 2 * p + 2;
       const unsigned long long s1 =
@@ -358,11 +348,43 @@ __global__ void __launch_bounds__(kThreads) k_adj_step_quad(const double* __rest
                          geo.nx + pull_src(x, -cx, geo.nx, geo.zgx);
       ha[s] = g[a1 * n + s1];
       hb[s] = g[a2 * n + s2];
+    }
+  }
+}
+
+// lambda of lane j's pairs at the node: read directly (FIRST, the last step) or
+// gathered from the mu of the step after it.
+template <bool FIRST, bool TUBE>
+__device__ __forceinline__ void quad_lambda(const double* __restrict__ in, int x, int y, int z, int j,
+                                            unsigned long long i, const AGeo& geo, const int (&cd)[3][3],
+                                            double (&la)[3], double (&lb)[3]) {
+  const unsigned long long n = geo.n;
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    const int p = j + 4 * s;
+    la[s] = lb[s] = 0.0;
+    if (p <= 8) {
+      const unsigned long long a1 = 2 * p + 1, a2 = 2 * p + 2;
+      const int cx = cd[s][0], cy = cd[s][1], cz = cd[s][2];
       la[s] = FIRST ? in[a1 * n + i] : gather_any<TUBE>(in + a1 * n, x, y, z, cx, cy, cz, geo);
       lb[s] = FIRST ? in[a2 * n + i] : gather_any<TUBE>(in + a2 * n, x, y, z, -cx, -cy, -cz, geo);
     }
   }
-  // ---- forward intermediates: moments over the four lanes, then the scalar chain
+}
+
+// The forward intermediates of the g collide at one node that its reverse step uses
+// (the recovered state of the pulled h, Eq. 10 and the recovery, and the MRT
+// non-equilibrium scalars): 15 values.
+struct QFwd {
+  double ux, uy, uz, sigma, is, u2, kg, geq0, ne, np, Mx, My, Mz, rsA, T00;
+};
+constexpr int kFwdFields = 15;
+
+// QFwd from the rest link h0 and lane j's pairs: moments summed over the node's four
+// lanes, then the scalar chain in every lane.
+template <bool MRT>
+__device__ __forceinline__ void quad_forward(double h0, const double (&ha)[3], const double (&hb)[3],
+                                             const int (&cd)[3][3], int j, QFwd& F) {
   double Sa = 0, Sd = 0, Mx = 0, My = 0, Mz = 0;
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
@@ -389,14 +411,55 @@ __global__ void __launch_bounds__(kThreads) k_adj_step_quad(const double* __rest
   const double P = sigma - T00;
   const double u2 = fma(ux, ux, fma(uy, uy, uz * uz));
   const double su2 = sigma * u2, P3 = 3.0 * P;
-  const double kg = fma(-1.5, su2, P3), geq0 = fma(-0.5, su2, sigma - P3);
-  double ne = 0, np = 0;
+  F.kg = fma(-1.5, su2, P3);
+  F.geq0 = fma(-0.5, su2, sigma - P3);
+  F.ne = F.np = 0.0;
   if (MRT) {
-    const double n0 = h0 - geq0, nA = Sa - P, nD = fma(-0.5, su2, Sd - P);
-    ne = fma(8.0, nD, fma(-11.0, nA, -30.0 * n0));
-    np = fma(-4.0, nA, fma(12.0, n0, nD));
+    const double n0 = h0 - F.geq0, nA = Sa - P, nD = fma(-0.5, su2, Sd - P);
+    F.ne = fma(8.0, nD, fma(-11.0, nA, -30.0 * n0));
+    F.np = fma(-4.0, nA, fma(12.0, n0, nD));
   }
-  // ---- reverse, per pair, then summed over the four lanes
+  F.ux = ux;
+  F.uy = uy;
+  F.uz = uz;
+  F.sigma = sigma;
+  F.is = is;
+  F.u2 = u2;
+  F.Mx = Mx;
+  F.My = My;
+  F.Mz = Mz;
+  F.rsA = rcp_seeded(sA);
+  F.T00 = T00;
+}
+
+// Stored QFwd of node i (field q at q * n + i).
+__device__ __forceinline__ void store_fwd(double* __restrict__ fw, unsigned long long i, unsigned long long n,
+                                          const QFwd& F) {
+  const double v[kFwdFields] = {F.ux, F.uy, F.uz, F.sigma, F.is, F.u2, F.kg, F.geq0,
+                                F.ne, F.np, F.Mx, F.My, F.Mz, F.rsA, F.T00};
+#pragma unroll
+  for (int q = 0; q < kFwdFields; ++q) fw[q * n + i] = v[q];
+}
+__device__ __forceinline__ void load_fwd(const double* __restrict__ fw, unsigned long long i, unsigned long long n,
+                                         QFwd& F) {
+  double v[kFwdFields];
+#pragma unroll
+  for (int q = 0; q < kFwdFields; ++q) v[q] = fw[q * n + i];
+  F.ux = v[0]; F.uy = v[1]; F.uz = v[2]; F.sigma = v[3]; F.is = v[4]; F.u2 = v[5]; F.kg = v[6]; F.geq0 = v[7];
+  F.ne = v[8]; F.np = v[9]; F.Mx = v[10]; F.My = v[11]; F.Mz = v[12]; F.rsA = v[13]; F.T00 = v[14];
+}
+
+// The reverse of the collide at one node in lane j: per-pair cotangents, sums over the
+// node's four lanes, the scalar chain backwards (MRT scalars, equilibria, recovery,
+// moments), then the stores of mu for lane j's pairs and, in lane 0, the rest link and
+// the omega contributions.
+template <bool MRT>
+__device__ __forceinline__ void quad_backward(const QFwd& F, double h0, double l0, const double (&ha)[3],
+                                              const double (&hb)[3], const double (&la)[3], const double (&lb)[3],
+                                              const int (&cd)[3][3], int j, bool valid, unsigned long long i,
+                                              const StepConst& k, double* __restrict__ mu, double* __restrict__ tb,
+                                              unsigned long long n) {
+  const double ux = F.ux, uy = F.uy, uz = F.uz, sigma = F.sigma, is = F.is;
   const double om = k.omv, om1 = k.omv1;
   const double wA = 1.0 / 18.0, wD = 1.0 / 36.0;
   const double SA2 = 2.0 * k.gA_s * sigma, SD2 = 2.0 * k.gD_s * sigma, AA = k.gA_a * sigma, AD = k.gD_a * sigma;
@@ -434,20 +497,20 @@ __global__ void __launch_bounds__(kThreads) k_adj_step_quad(const double* __rest
   uzb = quad_sum(uzb);
   // rest link: out0 = (1 - om) h0 + om geq0 (+ 30 ae - 12 ap)
   const double o0 = om1 * l0;
-  wvb += (geq0 - h0) * l0;
+  wvb += (F.geq0 - h0) * l0;
   double geq0b = om * l0;
   double aeb = 30.0 * l0, apb = -12.0 * l0;
   aeb += 11.0 * KAb - 8.0 * KDb;
   apb += 4.0 * KAb - KDb;
   const double kgb = om * (wA * KAb + wD * KDb);
-  wvb += kg * (wA * KAb + wD * KDb);
+  wvb += F.kg * (wA * KAb + wD * KDb);
   const double sw = 4.5 * (wA * SAb + wD * SDb) + 3.0 * (wA * AAb + wD * ADb);
   double sigmab = om * sw;
   wvb += sigma * sw;
   double Sab = 0, Sdb = 0, Pb = 0, su2b = 0, h0x = 0, web = 0, wpb = 0;
   if (MRT) {
     const double neb = k.ce * aeb, npb = k.cp * apb;
-    const double ceb = ne * aeb * (1.0 / 2394.0), cpb = np * apb * (1.0 / 252.0);
+    const double ceb = F.ne * aeb * (1.0 / 2394.0), cpb = F.np * apb * (1.0 / 252.0);
     web = ceb;
     wpb = cpb;
     wvb -= ceb + cpb;
@@ -465,7 +528,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_step_quad(const double* __rest
   sigmab += geq0b;
   su2b += -0.5 * geq0b - 1.5 * kgb;
   Pb += 3.0 * (kgb - geq0b);
-  sigmab += u2 * su2b;
+  sigmab += F.u2 * su2b;
   const double u2b = sigma * su2b;
   uxb += 2.0 * ux * u2b;
   uyb += 2.0 * uy * u2b;
@@ -474,14 +537,14 @@ __global__ void __launch_bounds__(kThreads) k_adj_step_quad(const double* __rest
   sigmab += Pb;
   double T00b = -Pb;
   double Mxb = is * uxb, Myb = is * uyb, Mzb = is * uzb;
-  sigmab -= is * is * (Mx * uxb + My * uyb + Mz * uzb);
+  sigmab -= is * is * (F.Mx * uxb + F.My * uyb + F.Mz * uzb);
   T00b += (2.0 / 3.0) * sigmab;
-  const double Ab = sigmab * (1.0 / 6.0) * rcp_seeded(sA);
-  T00b += 8.0 * T00 * Ab;
+  const double Ab = sigmab * (1.0 / 6.0) * F.rsA;
+  T00b += 8.0 * F.T00 * Ab;
   const double MMb = -6.0 * Ab;
-  Mxb += Mx * MMb;
-  Myb += My * MMb;
-  Mzb += Mz * MMb;
+  Mxb += F.Mx * MMb;
+  Myb += F.My * MMb;
+  Mzb += F.Mz * MMb;
   // T00 = h0 + Sa + Sd
   Sab += T00b;
   Sdb += T00b;
@@ -501,6 +564,64 @@ __global__ void __launch_bounds__(kThreads) k_adj_step_quad(const double* __rest
     tb[n + i] += web;
     tb[2 * n + i] += wpb;
   }
+}
+
+// ---- two warp roles (small lattices, the reverse sweep's chain)
+//
+// Nothing in QFwd depends on lambda, only on the forward state, so the reverse step
+// need not recompute it on its own dependent chain.  k_adj_step_ws runs 8 nodes per
+// 64-thread block: warp 0 walks the backward chain of step t from the QFwd stored for
+// step t (fw), and warp 1 computes and stores the QFwd of step t - 1 (from g_prev, the
+// state at step t - 1, into fw_prev) for the next launch.  k_adj_fwd stores the QFwd of
+// one step on its own (the last step, where the reverse sweep starts).
+template <bool MRT, bool TUBE>
+__global__ void __launch_bounds__(64) k_adj_fwd(const double* __restrict__ g, double* __restrict__ fw, AGeo geo) {
+  const int j = threadIdx.x & 3;
+  const int xg = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 2);
+  const bool valid = xg < geo.nx;
+  const int x = valid ? xg : geo.nx - 1;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const unsigned long long i = ((unsigned long long)z * geo.ny + y) * geo.nx + x;
+  double ha[3], hb[3];
+  int cd[3][3];
+  const double h0 = g[i];
+  quad_pull<TUBE>(g, x, y, z, j, geo, ha, hb, cd);
+  QFwd F;
+  quad_forward<MRT>(h0, ha, hb, cd, j, F);
+  if (valid && j == 0) store_fwd(fw, i, geo.n, F);
+}
+
+template <bool MRT, bool FIRST, bool TUBE>
+__global__ void __launch_bounds__(64) k_adj_step_ws(const double* __restrict__ g, const double* __restrict__ in,
+                                                    double* __restrict__ mu, double* __restrict__ tb,
+                                                    const double* __restrict__ fw, const double* __restrict__ g_prev,
+                                                    double* __restrict__ fw_prev, AGeo geo, StepConst k) {
+  const int lane = threadIdx.x & 31, j = lane & 3;
+  const int xg = (int)(blockIdx.x * 8 + (lane >> 2));
+  const bool valid = xg < geo.nx;
+  const int x = valid ? xg : geo.nx - 1;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const unsigned long long i = ((unsigned long long)z * geo.ny + y) * geo.nx + x;
+  double ha[3], hb[3];
+  int cd[3][3];
+  if (threadIdx.x >= 32) {
+    // step t - 1's forward intermediates (none before step 0)
+    if (g_prev == nullptr) return;
+    const double h0 = g_prev[i];
+    quad_pull<TUBE>(g_prev, x, y, z, j, geo, ha, hb, cd);
+    QFwd F;
+    quad_forward<MRT>(h0, ha, hb, cd, j, F);
+    if (valid && j == 0) store_fwd(fw_prev, i, geo.n, F);
+    return;
+  }
+  const double h0 = g[i];
+  const double l0 = in[i];
+  double la[3], lb[3];
+  quad_pull<TUBE>(g, x, y, z, j, geo, ha, hb, cd);
+  quad_lambda<FIRST, TUBE>(in, x, y, z, j, i, geo, cd, la, lb);
+  QFwd F;
+  load_fwd(fw, i, geo.n, F);
+  quad_backward<MRT>(F, h0, l0, ha, hb, la, lb, cd, j, valid, i, k, mu, tb, geo.n);
 }
 
 // lambda^T = dJ/dg^T and the per-node misfit.
@@ -581,6 +702,7 @@ struct AdjPlan {
   double wP = 0.0, wu = 0.0;                  // misfit weights baked into the graph
   std::vector<void*> ckpt, seg, segb, owned;     // seg / segb: the recomputed states of alternate segments
   double *lam = nullptr, *mu = nullptr, *tb = nullptr, *lossn = nullptr, *sums = nullptr, *dde0 = nullptr;
+  double* fw[2] = {nullptr, nullptr};         // QFwd of alternate reverse steps (two warp roles)
   double* tgt = nullptr;
   void* g0copy = nullptr;
   cudaStream_t cap = nullptr;
@@ -613,19 +735,20 @@ bool plan_alloc(AdjPlan* a, void** p, size_t bytes) {
   return true;
 }
 
-// One reverse step with the kernel variant for the lattice: four threads per node or
-// one, quasi-1D (ny = nz = 1) or general, BGK or MRT.
+// One reverse step with the kernel variant for the lattice: two warp roles with four
+// threads per node (quad; fw holds step t's QFwd, and step t - 1's goes from g_prev
+// into fw_prev) or one thread per node; quasi-1D (ny = nz = 1) or general; BGK or MRT.
 template <bool FIRST>
-cudaError_t reverse_step(bool quad, bool tube, bool mrt, dim3 grid4, dim3 grid3, int th, cudaStream_t st,
-                         const double* gt, const double* in, double* out, double* tb, const AGeo& geo,
-                         const StepConst& k, int lanes) {
+cudaError_t reverse_step(bool quad, bool tube, bool mrt, dim3 grid8, dim3 grid3, int th, cudaStream_t st,
+                         const double* gt, const double* in, double* out, double* tb, const double* fw,
+                         const double* g_prev, double* fw_prev, const AGeo& geo, const StepConst& k, int lanes) {
   if (quad) {
     if (tube) {
-      if (mrt) k_adj_step_quad<true, FIRST, true><<<grid4, th, 0, st>>>(gt, in, out, tb, geo, k);
-      else k_adj_step_quad<false, FIRST, true><<<grid4, th, 0, st>>>(gt, in, out, tb, geo, k);
+      if (mrt) k_adj_step_ws<true, FIRST, true><<<grid8, 64, 0, st>>>(gt, in, out, tb, fw, g_prev, fw_prev, geo, k);
+      else k_adj_step_ws<false, FIRST, true><<<grid8, 64, 0, st>>>(gt, in, out, tb, fw, g_prev, fw_prev, geo, k);
     } else {
-      if (mrt) k_adj_step_quad<true, FIRST><<<grid4, th, 0, st>>>(gt, in, out, tb, geo, k);
-      else k_adj_step_quad<false, FIRST><<<grid4, th, 0, st>>>(gt, in, out, tb, geo, k);
+      if (mrt) k_adj_step_ws<true, FIRST, false><<<grid8, 64, 0, st>>>(gt, in, out, tb, fw, g_prev, fw_prev, geo, k);
+      else k_adj_step_ws<false, FIRST, false><<<grid8, 64, 0, st>>>(gt, in, out, tb, fw, g_prev, fw_prev, geo, k);
     }
   } else if (tube) {
     if (mrt) k_adj_step<true, FIRST, true><<<grid3, th, 0, st>>>(gt, in, out, tb, geo, k, lanes);
@@ -645,7 +768,7 @@ cudaError_t enqueue_adjoint(rlb_handle* h, AdjPlan* a, double wP, double wu, boo
   const unsigned grid = (unsigned)((N + th - 1) / th);
   const int lanes = a->lanes;
   const dim3 grid3((unsigned)((h->cfg.nx + lanes - 1) / lanes), (unsigned)h->cfg.ny, (unsigned)h->cfg.nz);
-  const dim3 grid4((unsigned)((4ull * h->cfg.nx + th - 1) / th), (unsigned)h->cfg.ny, (unsigned)h->cfg.nz);
+  const dim3 grid8((unsigned)((h->cfg.nx + 7) / 8), (unsigned)h->cfg.ny, (unsigned)h->cfg.nz);
   double* mu_cur = nullptr;   // buffer holding the mu of the latest reverse step (lam / mu alternate)
   cudaStream_t st = a->cap;
   AGeo geo{h->cfg.nx, h->cfg.ny, h->cfg.nz, h->cfg.bc[0] == RLB_ZERO_GRADIENT, h->cfg.bc[1] == RLB_ZERO_GRADIENT,
@@ -701,15 +824,38 @@ cudaError_t enqueue_adjoint(rlb_handle* h, AdjPlan* a, double wP, double wu, boo
     ENQ(cudaStreamWaitEvent(st, ev_ready[s & 1], 0));
     const std::vector<void*>& b = *buf[s & 1];
     const int t0 = s * K, t1 = std::min(T, t0 + K);
+    if (a->quad && t1 == T) {   // the QFwd of the last step
+      if (tube) {
+        if (mrt) k_adj_fwd<true, true><<<grid8, 64, 0, st>>>((const double*)b[T - 1 - t0] + 19 * N, a->fw[(T - 1) & 1], geo);
+        else k_adj_fwd<false, true><<<grid8, 64, 0, st>>>((const double*)b[T - 1 - t0] + 19 * N, a->fw[(T - 1) & 1], geo);
+      } else {
+        if (mrt) k_adj_fwd<true, false><<<grid8, 64, 0, st>>>((const double*)b[T - 1 - t0] + 19 * N, a->fw[(T - 1) & 1], geo);
+        else k_adj_fwd<false, false><<<grid8, 64, 0, st>>>((const double*)b[T - 1 - t0] + 19 * N, a->fw[(T - 1) & 1], geo);
+      }
+      ENQ(cudaGetLastError());
+    }
     for (int t = t1 - 1; t >= t0; --t) {
       const double* gt = (const double*)b[t - t0] + 19 * N;
+      // the state at step t - 1: in this segment, else the top of the one below, whose
+      // recompute must have finished
+      const double* g_prev = nullptr;
+      if (t > t0) {
+        g_prev = (const double*)b[t - 1 - t0] + 19 * N;
+      } else if (s >= 1) {
+        ENQ(cudaStreamWaitEvent(st, ev_ready[(s - 1) & 1], 0));
+        g_prev = (const double*)(*buf[(s - 1) & 1])[K - 1] + 19 * N;
+      }
+      const double* fw = a->fw[t & 1];
+      double* fw_prev = a->fw[(t + 1) & 1];
       // the last step reads lambda^T; later ones gather from the mu of the step after
       double* out = mu_cur == a->mu ? a->lam : a->mu;
       if (t == T - 1) {
         out = a->mu;
-        ENQ(reverse_step<true>(a->quad, tube, mrt, grid4, grid3, th, st, gt, a->lam, out, a->tb, geo, h->k, lanes));
+        ENQ(reverse_step<true>(a->quad, tube, mrt, grid8, grid3, th, st, gt, a->lam, out, a->tb, fw, g_prev, fw_prev,
+                               geo, h->k, lanes));
       } else {
-        ENQ(reverse_step<false>(a->quad, tube, mrt, grid4, grid3, th, st, gt, mu_cur, out, a->tb, geo, h->k, lanes));
+        ENQ(reverse_step<false>(a->quad, tube, mrt, grid8, grid3, th, st, gt, mu_cur, out, a->tb, fw, g_prev, fw_prev,
+                                geo, h->k, lanes));
       }
       mu_cur = out;
     }
@@ -789,6 +935,7 @@ extern "C" int rlb_adjoint(rlb_handle* h, int nsteps, int checkpoint_every, cons
          plan_alloc(a, (void**)&a->tb, 3 * N * sizeof(double)) && plan_alloc(a, (void**)&a->lossn, N * sizeof(double)) &&
          plan_alloc(a, (void**)&a->sums, 8 * sizeof(double)) && plan_alloc(a, (void**)&a->dde0, N * sizeof(double)) &&
          plan_alloc(a, (void**)&a->tgt, 4 * N * sizeof(double)) && plan_alloc(a, &a->g0copy, state_bytes);
+    for (int i = 0; i < 2 && ok && a->quad; ++i) ok = plan_alloc(a, (void**)&a->fw[i], kFwdFields * N * sizeof(double));
     if (!ok || cudaStreamCreateWithFlags(&a->cap, cudaStreamNonBlocking) != cudaSuccess) {
       free_plan(a);
       return afail(h, RLB_ENOMEM, "cannot allocate adjoint checkpoints and buffers");
