@@ -943,16 +943,40 @@ __device__ __forceinline__ float pow2_bits(int e) {  // 2^(e - 127), e clamped t
   return __uint_as_float((unsigned)e << 23);
 }
 
-// Largest biased exponent of |p| over the 19 values (255 if any is Inf or NaN).
+// Largest biased exponent of |p| over the 19 values (255 if any is Inf or NaN).  On
+// magnitudes the float order is the order of the bit patterns, so the max runs as a
+// float max with |.| operands (max.NaN keeps a NaN, whose pattern has exponent 255)
+// instead of masking each pattern and comparing integers.
+#ifndef RLB_F32_FMNMX
+#define RLB_F32_FMNMX 1
+#endif
+__device__ __forceinline__ float fmax_keep_nan(float a, float b) {
+  float r;
+  asm("max.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  return r;
+}
 __device__ __forceinline__ int max_exp19(const float (&p)[19]) {
+  if (RLB_F32_FMNMX) {
+    float m = fabsf(p[0]);
+#pragma unroll
+    for (int a = 1; a < 19; ++a) m = fmax_keep_nan(m, fabsf(p[a]));
+    return (int)(__float_as_uint(m) >> 23);
+  }
   unsigned m = __float_as_uint(p[0]) & 0x7fffffffu;
 #pragma unroll
   for (int a = 1; a < 19; ++a) m = max(m, __float_as_uint(p[a]) & 0x7fffffffu);
   return (int)(m >> 23);
 }
 
-// Smallest biased exponent of |p| over the 19 values (0 if any is zero or subnormal).
+// Smallest biased exponent of |p| over the 19 values (0 if any is zero or subnormal;
+// a NaN is passed over, max_exp19 reports it).
 __device__ __forceinline__ int min_exp19(const float (&p)[19]) {
+  if (RLB_F32_FMNMX) {
+    float m = fabsf(p[0]);
+#pragma unroll
+    for (int a = 1; a < 19; ++a) m = fminf(m, fabsf(p[a]));
+    return (int)(__float_as_uint(m) >> 23);
+  }
   unsigned m = __float_as_uint(p[0]) & 0x7fffffffu;
 #pragma unroll
   for (int a = 1; a < 19; ++a) m = min(m, __float_as_uint(p[a]) & 0x7fffffffu);
