@@ -103,9 +103,9 @@ __device__ __forceinline__ void pull19(const S* __restrict__ base, unsigned long
 #ifndef RLB_F64_BLOCKS_PER_SM
 #define RLB_F64_BLOCKS_PER_SM 3
 #endif
-// and the FP32-storage step
+// and the FP32-storage step (6: 80 registers, none spilled)
 #ifndef RLB_F32_BLOCKS_PER_SM
-#define RLB_F32_BLOCKS_PER_SM 7
+#define RLB_F32_BLOCKS_PER_SM 6
 #endif
 
 template <typename S, bool MRT, bool QSEP, bool ETA = false>
