@@ -199,6 +199,20 @@ __device__ __forceinline__ float d2f_trunc_bits(double x) {   // seed only: trun
                      ((hi & 0xfffffu) << 3) | (lo >> 29);
   return __uint_as_float(b);
 }
+// the same with the result scaled by 2^es (seed arithmetic away from the FP32 range limits)
+__device__ __forceinline__ float d2f_trunc_bits_s(double x, int es) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const int e = (int)((hi >> 20) & 0x7ffu) - 896 + es;
+  const unsigned b = (hi & 0x80000000u) | ((unsigned)(e < 1 ? 1 : (e > 254 ? 254 : e)) << 23) |
+                     ((hi & 0xfffffu) << 3) | (lo >> 29);
+  return __uint_as_float(b);
+}
+__device__ __forceinline__ double widen_seed_s(float rf, int es) {   // normal float x 2^es -> double
+  const unsigned rb = __float_as_uint(rf);
+  return __hiloint2double(
+      (int)((rb & 0x80000000u) | ((((rb >> 23) & 0xffu) + 896u + (unsigned)es) << 20) | ((rb & 0x7fffffu) >> 3)),
+      (int)(rb << 29));
+}
 __device__ __forceinline__ double widen_seed(float rf) {   // normal float -> double by moving bits
   const unsigned rb = __float_as_uint(rf);
   return __hiloint2double((int)((rb & 0x80000000u) | ((((rb >> 23) & 0xffu) + 896u) << 20) | ((rb & 0x7fffffu) >> 3)),
@@ -1199,9 +1213,24 @@ __device__ __forceinline__ void f32s_g_recover(const float (&g)[19], G32& s) {
   const double Mzu = fx::from_fixed_int(KZ, 1079);
   const int eg = Eg - 183;
   const double MM = fma(Mxu, Mxu, fma(Myu, Myu, Mzu * Mzu));
-  const double A = fma(scale_pow2(Tu, 2), Tu, -3.0 * MM);
-  const double sgu = fma(2.0, Tu, sqrt_seeded(A)) * (1.0 / 3.0);
-  const double is = rcp_seeded(sgu);
+  // sigma is the larger root of 3 s^2 - 4 T00 s + |M|^2 = 0 (Eq. 10 inverted): an FP32
+  // seed s0 from the closed form on values scaled by 2^-64, then one Newton step on the
+  // quadratic in FP64, s0 - q(s0) / q'(s0), with q'(s0) = 6 s0 - 4 T00 taken in FP32
+  // (relative error about 2^-42, far below the FP32 rounding of everything it feeds);
+  // 1 / sigma from an FP32 seed and one Newton step
+  const float tf = d2f_trunc_bits_s(Tu, -64), xf = d2f_trunc_bits_s(Mxu, -64);
+  const float yf = d2f_trunc_bits_s(Myu, -64), zf = d2f_trunc_bits_s(Mzu, -64);
+  const float Af = fmaf(4.0f * tf, tf, -3.0f * fmaf(xf, xf, fmaf(yf, yf, zf * zf)));
+  float rA, r0;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(rA) : "f"(Af));
+  const float s0f = fmaf(2.0f, tf, rA) * (1.0f / 3.0f);
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rA) : "f"(fmaf(6.0f, s0f, -4.0f * tf)));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(s0f));
+  const double s0 = widen_seed_s(s0f, 64);
+  const double q = fma(s0, fma(3.0, s0, -scale_pow2(Tu, 2)), MM);
+  const double sgu = fma(-q, widen_seed_s(rA, -64), s0);
+  const double y = widen_seed_s(r0, -64);
+  const double is = fma(y, fma(-sgu, y, 1.0), y);
   const double Pu = sgu - Tu;
   // per-node equilibrium constants (they cancel, sigma ~ 4P): FP64, then one rounding;
   // sigma u^2 = |M|^2 / sigma
@@ -1226,8 +1255,8 @@ __device__ __forceinline__ void f32s_g_recover(const float (&g)[19], G32& s) {
     s.Mz = d2f_rn_bits_scaled(Mzu, eg);
   }
   const float u2 = fmaf(s.ux, s.ux, fmaf(s.uy, s.uy, s.uz * s.uz));
-  // A > 0, T00 > 0, P > 0 (all finite), u^2 < 1 (on the rounded velocity; NaN fails)
-  s.bad = !(pos_finite_hi(A) && pos_finite_hi(Tu) && pos_finite_hi(Pu) && u2 < 1.0f) || Eg == 255;
+  // A > 0 (its FP32 seed value), T00 > 0, P > 0 (finite), u^2 < 1 (on the rounded velocity; NaN fails)
+  s.bad = !(Af > 0.0f && pos_finite_hi(Tu) && pos_finite_hi(Pu) && u2 < 1.0f) || Eg == 255;
 }
 
 template <bool MRT, bool QSEP>
