@@ -83,10 +83,10 @@ NCU_BYTES_PER_UPDATE = {"fp64": (638868224 + 626036736) / 2097152, "fp32": 587.7
 NCU_BYTES_PER_UPDATE_TUBES = 52.044659e9 / (1719757 * 200)
 
 # FP64-pipe operations of one FP32-storage node update (the sums are exact on the
-# FP32 and integer pipes and rounded to FP64 by integer bit assembly): recovery 20
-# (|M|^2 3, A 2, sqrt 6, sigma 2, reciprocal 3, u 3, P 1) + sigma u^2 1 +
-# equilibrium constants 4.
-FP64_OPS_PER_UPDATE_F32S = 25
+# FP32 and integer pipes and rounded to FP64 by integer bit assembly): recovery 15
+# (|M|^2 3, quadratic residual 2, Newton step 1, reciprocal 2, u 3 and its 3
+# conversions to FP32, P 1) + sigma u^2 1 + equilibrium constants 4.
+FP64_OPS_PER_UPDATE_F32S = 20
 
 # FP64-pipe operations (int64 -> FP64 conversion = 1) of one FP64 node update: the 38
 # roundings of the relaxed links.  The sums, the recovery, the equilibria and the
@@ -259,7 +259,11 @@ def run_tubes(args, dist, rank, ws, local):
     stream = torch.cuda.Stream()
     b = TubeBatch(lengths, taus, precision="fp32", stream=stream)
     b.set_fields(*[t.cuda() for t in fields])
-    shape = b.autotune(16)
+    if args.tubes_shape:
+        shape = tuple(int(v) for v in args.tubes_shape.split(","))
+        b.set_shape(*shape)
+    else:
+        shape = b.autotune(16)
     b.run(args.warmup)
     b.check()
     b.set_fields(*[t.cuda() for t in fields])
@@ -589,6 +593,8 @@ def main():
                     help="box workloads: at least this many timed regions of --steps steps (median reported)")
     ap.add_argument("--min-seconds", type=float, default=2.0,
                     help="box workloads: repeat timed regions until this much device time has passed")
+    ap.add_argument("--tubes-shape", default=None,
+                    help="threads,ctas_per_sm for the tube sweep instead of autotuning (for profiling)")
     ap.add_argument("--no-fp32-storage", action="store_true",
                     help="default workload only: skip the nested FP32-storage 512^3 box")
     ap.add_argument("--ref-seconds", type=float, default=20.0,

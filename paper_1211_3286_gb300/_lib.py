@@ -81,6 +81,7 @@ def load():
         "rlb_batch_offset": (ctypes.c_size_t, [_P, ctypes.c_int]),
         "rlb_batch_set_fields": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, ctypes.c_int]),
         "rlb_batch_autotune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+        "rlb_batch_set_shape": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
         "rlb_batch_run": (ctypes.c_int, [_P, ctypes.c_int]),
         "rlb_batch_check": (ctypes.c_int, [_P]),
         "rlb_batch_get_fields": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, ctypes.c_int]),
@@ -103,7 +104,7 @@ def exported_symbols():
             "rlb_get_fields", "rlb_conserved_totals", "rlb_state_bytes", "rlb_save_state", "rlb_load_state",
             "rlb_steps_done", "rlb_conserved_totals_noalloc",
             "rlb_batch_create", "rlb_batch_destroy", "rlb_batch_last_error", "rlb_batch_nodes", "rlb_batch_offset",
-            "rlb_batch_set_fields", "rlb_batch_autotune", "rlb_batch_run", "rlb_batch_check", "rlb_batch_get_fields",
+            "rlb_batch_set_fields", "rlb_batch_autotune", "rlb_batch_set_shape", "rlb_batch_run", "rlb_batch_check", "rlb_batch_get_fields",
             "rlb_batch_state_bytes", "rlb_batch_save_state", "rlb_batch_load_state", "rlb_adjoint"]
 
 
@@ -212,6 +213,10 @@ def rlb_batch_autotune(b, trial_steps):
     ch = (ctypes.c_int * 2)()
     _bcheck(load().rlb_batch_autotune(b, int(trial_steps), ch), b)
     return int(ch[0]), int(ch[1])
+
+
+def rlb_batch_set_shape(b, threads, ctas_per_sm):
+    _bcheck(load().rlb_batch_set_shape(b, int(threads), int(ctas_per_sm)), b)
 
 
 def rlb_batch_run(b, nsteps):

@@ -59,6 +59,9 @@ class TubeBatch:
     def autotune(self, trial_steps=32):
         return L.rlb_batch_autotune(self._b, trial_steps)
 
+    def set_shape(self, threads, ctas_per_sm=0):
+        L.rlb_batch_set_shape(self._b, threads, ctas_per_sm)
+
     def run(self, nsteps):
         L.rlb_batch_run(self._b, nsteps)
 

@@ -522,6 +522,28 @@ extern "C" int rlb_batch_autotune(rlb_batch* b, int trial_steps, int* chosen) {
   return RLB_OK;
 }
 
+extern "C" int rlb_batch_set_shape(rlb_batch* b, int threads, int ctas_per_sm) {
+  if (!b) return bfail(b, RLB_EINVAL, "null batch");
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, tube_kernel(b)) != cudaSuccess) {
+    cudaGetLastError();
+    return bfail(b, RLB_ECUDA, "cannot query the tube kernel");
+  }
+  if (threads < 32 || threads % 32 != 0 || threads > fa.maxThreadsPerBlock)
+    return bfail(b, RLB_EINVAL, "threads must be a multiple of 32 up to " + std::to_string(fa.maxThreadsPerBlock));
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tube_kernel(b), threads, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return bfail(b, RLB_ECUDA, "cannot query the occupancy of the tube kernel");
+  }
+  if (ctas_per_sm < 0 || ctas_per_sm > occ)
+    return bfail(b, RLB_EINVAL, "ctas_per_sm must be 0 to " + std::to_string(occ) + " at " +
+                                    std::to_string(threads) + " threads");
+  b->threads = threads;
+  b->ctas_per_sm = ctas_per_sm;
+  return RLB_OK;
+}
+
 extern "C" int rlb_batch_run(rlb_batch* b, int nsteps) {
   if (!b) return bfail(b, RLB_EINVAL, "null batch");
   if (nsteps < 0) return bfail(b, RLB_EINVAL, "nsteps must be >= 0");

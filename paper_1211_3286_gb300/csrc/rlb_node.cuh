@@ -1089,7 +1089,11 @@ __device__ __forceinline__ long long levels_to_int(const float (&v)[3], int E) {
   return LV > 2 ? k12 + level_int(v[2], E - 56) : k12;
 }
 
-// Two-level fast path of the exact sums, read back as integers on the FP32 pipe.  At
+// Two-level fast path of the exact sums, read back as integers on the FP32 pipe.  The
+// first level splits each value x into q1, a multiple of 2^(E - 145), and the remainder
+// r1 = x - q1 (both exact, |r1| <= 2^(E - 145)); when every value's exponent is at least
+// E - 13 its last bit is at least 2^(E - 163), so r1 already lies on the second level's
+// grid and is its part (the second extraction would return it unchanged).  At
 // level L (grid unit u_L = 2^(E - 145 - 19 (L - 1))) every extracted part q is k u_L
 // with |k| <= 2^19, so a sum S of at most 8 parts is k u_L with |k| <= 2^22; then
 // S + C, C = 1.5 2^23 u_L, is exact and lies in C's binade or at its upper edge, where
@@ -1105,7 +1109,7 @@ __device__ __forceinline__ int group_int(float S, float C) {
 }
 __device__ __forceinline__ void exact_ints_g2(const float (&g)[19], int E, long long& KT, long long& KX,
                                               long long& KY, long long& KZ, float& Sa, float& Sd) {
-  const float sg[2] = {pow2_bits(E + 6), pow2_bits(E - 13)};
+  const float sg = pow2_bits(E + 6);
   const float C[2] = {__uint_as_float(((unsigned)(E + 5) << 23) | 0x400000u),
                       __uint_as_float(((unsigned)(E - 14) << 23) | 0x400000u)};
   float r[19];
@@ -1119,9 +1123,13 @@ __device__ __forceinline__ void exact_ints_g2(const float (&g)[19], int E, long 
     float q[19];
 #pragma unroll
     for (int a = 0; a < 19; ++a) {
-      const float t = sg[L] + r[a];
-      q[a] = t - sg[L];
-      r[a] = r[a] - q[a];
+      if (L == 0) {
+        const float t = sg + r[a];
+        q[a] = t - sg;
+        r[a] = r[a] - q[a];
+      } else {
+        q[a] = r[a];   // the second level's parts are the first level's remainders
+      }
     }
     float sp[9], dp[9];
 #pragma unroll
@@ -1144,7 +1152,7 @@ __device__ __forceinline__ void exact_ints_g2(const float (&g)[19], int E, long 
   KZ = (((long long)kZ[0] << 19) + kZ[1]) << 19;
 }
 __device__ __forceinline__ long long exact_int_f2(const float (&f)[19], int E) {
-  const float sg[2] = {pow2_bits(E + 6), pow2_bits(E - 13)};
+  const float sg = pow2_bits(E + 6);
   const float C[2] = {__uint_as_float(((unsigned)(E + 5) << 23) | 0x400000u),
                       __uint_as_float(((unsigned)(E - 14) << 23) | 0x400000u)};
   float r[19];
@@ -1156,9 +1164,13 @@ __device__ __forceinline__ long long exact_int_f2(const float (&f)[19], int E) {
     float q[19];
 #pragma unroll
     for (int a = 0; a < 19; ++a) {
-      const float t = sg[L] + r[a];
-      q[a] = t - sg[L];
-      r[a] = r[a] - q[a];
+      if (L == 0) {
+        const float t = sg + r[a];
+        q[a] = t - sg;
+        r[a] = r[a] - q[a];
+      } else {
+        q[a] = r[a];
+      }
     }
     const float s1 = ((q[0] + q[1]) + (q[2] + q[3])) + ((q[4] + q[5]) + q[6]);
     const float s2 = ((q[7] + q[8]) + (q[9] + q[10])) + (q[11] + q[12]);
@@ -1239,9 +1251,11 @@ __device__ __forceinline__ void f32s_g_recover(const float (&g)[19], G32& s) {
   s.su2 = d2f_rn_bits_scaled(su2u, eg);
   s.kg = d2f_rn_bits_scaled(fma(-1.5, su2u, P3u), eg);
   s.geq0 = d2f_rn_bits_scaled(fma(-0.5, su2u, sgu - P3u), eg);
-  s.ux = d2f_rn_bits(Mxu * is);
-  s.uy = d2f_rn_bits(Myu * is);
-  s.uz = d2f_rn_bits(Mzu * is);
+  // u to FP32 by the FP64 pipe's conversion (round to nearest; the other narrowings
+  // stay on the integer pipes, which carry more of this kernel's work)
+  s.ux = __double2float_rn(Mxu * is);
+  s.uy = __double2float_rn(Myu * is);
+  s.uz = __double2float_rn(Mzu * is);
   s.sg = d2f_rn_bits_scaled(sgu, eg);
   s.P = d2f_rn_bits_scaled(Pu, eg);
   if (MRT) {

@@ -122,6 +122,18 @@ def test_autotune_and_graph_replay_do_not_change_results():
     assert torch.equal(b.state(), sa)
     a.close()
     b.close()
+    # a pinned shape (no timing) gives the same state; shapes outside the launch
+    # bound or the occupancy limit are refused and leave the batch usable
+    from paper_1211_3286_gb300._lib import RlbError
+    d = TubeBatch(lengths, taus, precision="fp32")
+    d.set_fields(*f)
+    for bad in ((48, 1), (0, 1), (1024, 1), (64, -1), (64, 1000)):
+        with pytest.raises(RlbError):
+            d.set_shape(*bad)
+    d.set_shape(96, 2)
+    d.run(60)
+    assert torch.equal(d.state(), sa)
+    d.close()
     # FP64 tubes take at most 256 threads per CTA: larger candidates are skipped cleanly
     c = TubeBatch(lengths[:5], taus[:5], precision="fp64")
     c.set_fields(*_batch_fields(lengths[:5]))
