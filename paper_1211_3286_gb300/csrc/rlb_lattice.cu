@@ -76,11 +76,27 @@ __device__ __forceinline__ int src_plus(int i, int n, int zg) {   // source of a
 #endif
 template <typename S>
 __device__ __forceinline__ S ldg_nc(const S* p) { return __ldg(p); }
+// L2 prefetch size of the population loads: 256 B, the row segment a warp reads
+// (512^3 FP32 step 6.763 -> 6.740 ms, 256^3 FP64 step 1.859 -> 1.856 ms)
+#ifndef RLB_LD_PF
+#define RLB_LD_PF 256
+#endif
 #if RLB_LD_NOALLOC
 template <>
 __device__ __forceinline__ double ldg_nc<double>(const double* p) {
   double v;
-  asm("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  if (RLB_LD_PF == 256) asm("ld.global.nc.L1::no_allocate.L2::256B.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  else if (RLB_LD_PF == 128) asm("ld.global.nc.L1::no_allocate.L2::128B.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  else asm("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
+#endif
+#if RLB_LD_PF
+template <>
+__device__ __forceinline__ float ldg_nc<float>(const float* p) {
+  float v;
+  if (RLB_LD_PF == 256) asm("ld.global.nc.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  else asm("ld.global.nc.L2::128B.f32 %0, [%1];" : "=f"(v) : "l"(p));
   return v;
 }
 #endif
