@@ -75,12 +75,12 @@ DEFAULT_STEPS = {"box256": 500, "box128": 500, "box128_fp32": 500, "box512_fp32"
 # DRAM bytes (read + write) per node update of the step kernel, from ncu captures of the
 # 128^3 box with the same kernel (the 256^3 / 512^3 lattices exceed the capture size
 # rule); traffic per launch = bytes per update x nodes.  profiles/k_step_ws_box128_f64.md:
-# 638.9 MB read + 626.0 MB written / 2,097,152; profiles/k_step_box128_f32.md: 587.7 MB /
-# 2,097,152.
-NCU_BYTES_PER_UPDATE = {"fp64": (638868224 + 626036736) / 2097152, "fp32": 587.74784e6 / 2097152}
-# k_tubes on the 1024-tube sweep (profiles/k_tubes_sweep1024_fp32.md): 52.04 GB over
-# 1,719,757 nodes x 200 steps
-NCU_BYTES_PER_UPDATE_TUBES = 52.044659e9 / (1719757 * 200)
+# 639.4 MB read + 626.3 MB written / 2,097,152; profiles/k_step_box128_f32.md: 318.8 MB
+# read + 268.1 MB written / 2,097,152.
+NCU_BYTES_PER_UPDATE = {"fp64": (639426304 + 626273536) / 2097152, "fp32": (318828032 + 268112384) / 2097152}
+# k_tubes on the 1024-tube sweep at 256 threads x 3 CTAs per SM
+# (profiles/k_tubes_sweep1024_fp32.md): 79.16 GB over 1,719,757 nodes x 200 steps
+NCU_BYTES_PER_UPDATE_TUBES = (34.264691e9 + 44.898400e9) / (1719757 * 200)
 
 # FP64-pipe operations of one FP32-storage node update (the sums are exact on the
 # FP32 and integer pipes and rounded to FP64 by integer bit assembly): recovery 15
