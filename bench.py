@@ -28,6 +28,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -391,8 +392,17 @@ def run_adjoint(args, dist, rank, ws, local):
                 "config": {"workload": wl["desc"], "ms_per_gradient": dt * 1e3, "loss": loss,
                            "dtau": dtau.tolist(), "value_counts": "forward node updates per second of a full "
                            "gradient (forward + recompute + reverse)"},
-                "clocks": cs.summary(), "e2e": None, "gpu_launches": 5 * T}
+                "clocks": cs.summary(), "e2e": None, "gpu_launches": reps * adjoint_launches(T)}
         print(json.dumps(line))
+
+
+def adjoint_launches(T):
+    """librlb kernels of one gradient on the 1600-node tube: k_init (set_fields); T forward
+    steps; k_adj_loss; k_adj_fwd; T - nseg recompute steps (segments of K = ceil(sqrt T)
+    steps, each refilled from its checkpoint); T reverse steps; k_adj_e0; two k_rowsum."""
+    K = max(1, math.ceil(math.sqrt(T)))
+    nseg = (T + K - 1) // K
+    return 1 + T + 1 + 1 + (T - nseg) + T + 1 + 2
 
 
 def time_box(args, wl, steps, dist, ws, local, min_repeats=5, min_seconds=2.0, e2e=True):
