@@ -387,6 +387,20 @@ def test_moderately_relativistic_shock_fp64(collision):
     assert float(gpu["ux"].max()) > 0.5
 
 
+def test_moderately_relativistic_shock_fp32_storage():
+    """The same shock with FP32 population storage: plateau speed ~0.54, where the
+    recovery's one Newton step on sigma's quadratic meets its largest gamma^2 of the
+    tests; fields within the FP32 storage bound 50 x 2^-24 x sqrt(T) of the oracle."""
+    e, ux, uy, uz, n = (torch.from_numpy(a) for a in I.shock_tube(600, **I.MODERATE))
+    te = 0.5 + 2.5 / 30.0
+    T = 300
+    gpu, ref, _, _ = _run_both(e, ux, uy, uz, n, T, "mrt", (3.0, 3.0, te, te, 0.0),
+                               ("zero_gradient", "periodic", "periodic"), precision="fp32")
+    err = field_errors(gpu, ref)
+    assert max(err.values()) < 50 * 2.0 ** -24 * math.sqrt(T), err
+    assert float(gpu["ux"].max()) > 0.5
+
+
 def test_moderately_relativistic_breakdown_flagged_like_the_oracle():
     """tau_v = 1.5 with a = 1/30: the oracle meets a non-physical node; the GPU reports
     RLB_ENONPHYS within the same run (the device flag, no fault)."""
