@@ -9,7 +9,8 @@
 // inside the same kernel: the adjoint of "node x pulls link a from src(x)" is "node y
 // collects link a from every x with src(x) = y" -- one node for a periodic axis, and
 // for a zero-gradient axis also the edge node's own clamped pull.  Small lattices run
-// the reverse step with four threads per node (k_adj_step_quad), larger ones with one.
+// the reverse step with four threads per node in two warp roles (k_adj_step_ws), larger
+// ones with one thread per node (k_adj_step).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -294,7 +295,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_step(const double* __restrict_
 // ---- four threads per node (small lattices)
 //
 // On a lattice of a few thousand nodes one thread per node leaves each SM with a
-// single warp whose reverse step is one long dependent chain.  k_adj_step_quad gives
+// single warp whose reverse step is one long dependent chain.  The helpers below give
 // each node four lanes of a warp: lane j takes link pairs j, j + 4 and j + 8 (the rest
 // link is read by all four), the moments and the per-pair cotangents are summed over
 // the four lanes with xor shuffles, and the short scalar chains (recovery forward and

@@ -39,8 +39,8 @@
 //     -- the FP64 step with constant relaxation times;
 //   node_collide_f64: the same update in FP64 arithmetic -- the fixed-eta/s
 //     mode, whose relaxation times vary per node;
-//   node_collide_f32s: FP32 population storage, exact sums, FP64 recovery,
-//     FP32 per-link work;
+//   node_collide_f32s: FP32 population storage, exact sums, recovery by one FP64
+//     Newton step on sigma's quadratic from an FP32 seed, FP32 per-link work;
 //   node_collide_d2q9_f64: the D2Q9 model of Sec. V.A.
 #pragma once
 #include <cmath>

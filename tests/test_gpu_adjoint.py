@@ -167,7 +167,7 @@ def test_config5_1600_nodes_4000_steps_vs_central_differences():
 
 
 @pytest.mark.parametrize("shape, kind, T, K", [
-    ((1, 1, 400), "tube", 400, 100),     # four lanes per node (k_adj_step_quad), 4 segments
+    ((1, 1, 400), "tube", 400, 100),     # four lanes per node, two warp roles (k_adj_step_ws), 4 segments
     ((1, 1, 1600), "tube", 200, 50),     # four lanes per node, 4 segments
     ((4, 100, 100), "box", 12, 4),       # one thread per node (k_adj_step: > 38,912 nodes), 3 segments
 ])
