@@ -86,8 +86,8 @@ NCU_BYTES_PER_UPDATE_TUBES = (34.264691e9 + 44.898400e9) / (1719757 * 200)
 # FP64-pipe operations of one FP32-storage node update (the sums are exact on the
 # FP32 and integer pipes and rounded to FP64 by integer bit assembly): recovery 15
 # (|M|^2 3, quadratic residual 2, Newton step 1, reciprocal 2, u 3 and its 3
-# conversions to FP32, P 1) + sigma u^2 1 + equilibrium constants 4.
-FP64_OPS_PER_UPDATE_F32S = 20
+# conversions to FP32, P 1) + the three equilibrium constants 3.
+FP64_OPS_PER_UPDATE_F32S = 18
 
 # FP64-pipe operations (int64 -> FP64 conversion = 1) of one FP64 node update: the 38
 # roundings of the relaxed links.  The sums, the recovery, the equilibria and the

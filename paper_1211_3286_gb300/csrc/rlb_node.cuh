@@ -127,7 +127,9 @@ inline StepConst make_step_const(double tau_f, double tau_v, double tau_e, doubl
   k.fA_k_f = (float)k.fA_k; k.fD_k_f = (float)k.fD_k; k.f0_k_f = (float)k.f0_k;
   k.fA_s_f = (float)k.fA_s; k.fD_s_f = (float)k.fD_s; k.fA_a_f = (float)k.fA_a; k.fD_a_f = (float)k.fD_a;
   k.omv_f = (float)k.omv; k.omv1_f = (float)k.omv1;
-  k.gA_k_f = (float)k.gA_k; k.gD_k_f = (float)k.gD_k;
+  // the FP32-storage collide applies these to sigma u^2 - 2P = -(3P - 1.5 sigma u^2) / 1.5
+  k.gA_k_f = (float)(-1.5 * k.gA_k);
+  k.gD_k_f = (float)(-1.5 * k.gD_k);
   k.gA_s_f = (float)k.gA_s; k.gD_s_f = (float)k.gD_s; k.gA_a_f = (float)k.gA_a; k.gD_a_f = (float)k.gD_a;
   k.ce_f = (float)k.ce; k.cp_f = (float)k.cp; k.cq_f = (float)k.cq;
   k.Om_f = (unsigned long long)std::ldexp(k.omf, 63) & ~1ull;
@@ -1185,7 +1187,8 @@ __device__ __forceinline__ long long exact_int_f2(const float (&f)[19], int E) {
 // relaxation in FP32 with one rounding on store.  Split into the g part (sums,
 // recovery, g relaxation) and the f part (N0, f relaxation), which share only u.
 struct G32 {
-  float sg, P, su2, kg, geq0;   // sigma, P, sigma u^2, 3P - 1.5 sigma u^2, g^eq_0
+  float sg, P, su2, kg, geq0;   // sigma, P, sigma u^2, sigma u^2 - 2P (= -(3P - 1.5 sigma u^2) / 1.5),
+                                // g^eq_0
   float Sa, Sd;                 // axis / diagonal class sums of g (MRT)
   float Mx, My, Mz;             // momentum (energy-flux rows)
   float ux, uy, uz;
@@ -1239,18 +1242,21 @@ __device__ __forceinline__ void f32s_g_recover(const float (&g)[19], G32& s) {
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rA) : "f"(fmaf(6.0f, s0f, -4.0f * tf)));
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(s0f));
   const double s0 = widen_seed_s(s0f, 64);
-  const double q = fma(s0, fma(3.0, s0, -scale_pow2(Tu, 2)), MM);
+  const double T4 = scale_pow2(Tu, 2);
+  const double q = fma(s0, fma(3.0, s0, -T4), MM);
   const double sgu = fma(-q, widen_seed_s(rA, -64), s0);
   const double y = widen_seed_s(r0, -64);
   const double is = fma(y, fma(-sgu, y, 1.0), y);
   const double Pu = sgu - Tu;
   // per-node equilibrium constants (they cancel, sigma ~ 4P): FP64, then one rounding;
-  // sigma u^2 = |M|^2 / sigma
-  const double su2u = MM * is;
-  const double P3u = 3.0 * Pu;
+  // at the root |M|^2 / sigma = 4 T00 - 3 sigma, so the constants are linear in sigma
+  // and T00: sigma u^2 = 4 T00 - 3 sigma; sigma u^2 - 2P, the equilibria's
+  // 3P - 1.5 sigma u^2 over -1.5 (the FP32 constants carry the factor); and
+  // g^eq_0 = sigma - 3P - sigma u^2 / 2 = T00 - sigma / 2
+  const double su2u = fma(-3.0, sgu, T4);
   s.su2 = d2f_rn_bits_scaled(su2u, eg);
-  s.kg = d2f_rn_bits_scaled(fma(-1.5, su2u, P3u), eg);
-  s.geq0 = d2f_rn_bits_scaled(fma(-0.5, su2u, sgu - P3u), eg);
+  s.kg = d2f_rn_bits_scaled(fma(-2.0, Pu, su2u), eg);
+  s.geq0 = d2f_rn_bits_scaled(fma(-0.5, sgu, Tu), eg);
   // u to FP32 by the FP64 pipe's conversion (round to nearest; the other narrowings
   // stay on the integer pipes, which carry more of this kernel's work)
   s.ux = __double2float_rn(Mxu * is);

@@ -9,7 +9,9 @@ FP64, and recovers sigma as the larger root of 3 s^2 - 4 T00 s + |M|^2 = 0:
   q(s0) = s0 (3 s0 - 4 T00) + |M|^2 (FP64 fused multiply-adds) and 1 / q'(s0) an FP32
   reciprocal of 6 s0 - 4 t;
 * 1 / sigma from an FP32 reciprocal of s0 and one Newton step in FP64;
-* u = M / sigma and P = sigma - T00 in FP64.
+* u = M / sigma and P = sigma - T00 in FP64;
+* the equilibrium constants from the identity |M|^2 / sigma = 4 T00 - 3 sigma at the
+  root: sigma u^2 = 4 T00 - 3 sigma, sigma u^2 - 2P, and g^eq_0 = T00 - sigma / 2.
 
 This test restates that recipe in Python (FP32 operations through numpy float32, the
 FP64 fused multiply-add exactly through fractions) and checks it against the closed form
@@ -18,11 +20,13 @@ GPU's approximate sqrt and reciprocal are covered by perturbing each seed by up 
 several times their error.  With such seeds:
 
 * sigma is within 2^-40 (relative), and P = sigma - T00 within 2^-40 of sigma;
-* 1 / sigma is within 2^-38, and u within 2^-38 of max(|u|, 1e-3) per component.
+* 1 / sigma is within 2^-38, and u within 2^-38 of max(|u|, 1e-3) per component;
+* the three constants are within 2^-38 of sigma.
 
 Every one of these values is rounded to FP32 (2^-24) before the per-link work, so the
 bound leaves at least 14 bits of margin.  Planted mistakes each fail it: no Newton step,
-a wrong derivative, a wrong constant term.  The test runs no GPU code.
+a wrong derivative, a wrong constant term, a wrong sign in g^eq_0.  The test runs no GPU
+code.
 """
 import math
 import random
@@ -62,7 +66,7 @@ def recover(T, Mx, My, Mz, p=(0, 0, 0), plant=None):
     Af = f32(f32(4.0) * tf * tf - f32(3.0) * mm)
     if not Af > 0:                                     # flagged non-physical; the values are not used
         nan = float("nan")
-        return False, nan, nan, [nan] * 3, nan
+        return False, nan, nan, [nan] * 3, nan, (nan,) * 3
     rA = ulp_shift(f32(np.sqrt(Af)), p[0])
     s0f = f32(f32(f32(2.0) * tf + rA) * f32(1.0 / 3.0))
     rq = ulp_shift(f32(f32(1.0) / f32(f32(6.0) * s0f - f32(4.0) * tf)), p[1])
@@ -76,15 +80,22 @@ def recover(T, Mx, My, Mz, p=(0, 0, 0), plant=None):
     y = math.ldexp(float(r0), -64)
     inv = fma(y, fma(-sig, y, 1.0), y)
     u = [v * inv for v in (Mx, My, Mz)]
-    return Af > 0, sig, inv, u, sig - T
+    P = sig - T
+    su2 = fma(-3.0, sig, 4.0 * T)
+    kq = fma(-2.0, P, su2)
+    geq0 = fma(0.5 if plant == "geq0" else -0.5, sig, T)
+    return Af > 0, sig, inv, u, P, (su2, kq, geq0)
 
 
 def exact(T, M):
     getcontext().prec = 60
     Td = Decimal(T)
     Md = [Decimal(v) for v in M]
-    sig = (2 * Td + (4 * Td * Td - 3 * sum(v * v for v in Md)).sqrt()) / 3
-    return sig, 1 / sig, [v / sig for v in Md], sig - Td
+    MM = sum(v * v for v in Md)
+    sig = (2 * Td + (4 * Td * Td - 3 * MM).sqrt()) / 3
+    P = sig - Td
+    su2 = MM / sig                                   # sigma u^2 from its definition
+    return sig, 1 / sig, [v / sig for v in Md], P, (su2, su2 - 2 * P, sig - 3 * P - su2 / 2)
 
 
 def _states(n, seed):
@@ -105,34 +116,35 @@ def _states(n, seed):
 
 
 def _errors(T, M, p, plant=None):
-    ok, sig, inv, u, P = recover(T, *M, p=p, plant=plant)
-    es, ei, eu, eP = exact(T, M)
+    ok, sig, inv, u, P, c = recover(T, *M, p=p, plant=plant)
+    es, ei, eu, eP, ec = exact(T, M)
     e_sig = abs(Decimal(sig) - es) / es
     e_inv = abs(Decimal(inv) - ei) / ei
     umax = max(max(abs(v) for v in eu), Decimal("1e-3"))
     e_u = max(abs(Decimal(a) - b) for a, b in zip(u, eu)) / umax
     e_P = abs(Decimal(P) - eP) / es
-    return ok, float(e_sig), float(e_inv), float(e_u), float(e_P)
+    e_c = max(abs(Decimal(a) - b) for a, b in zip(c, ec)) / es
+    return ok, float(e_sig), float(e_inv), float(e_u), float(e_P), float(e_c)
 
 
 def test_fp32_storage_recovery_error_bound():
-    worst = [0.0, 0.0, 0.0, 0.0]                     # sigma, 1/sigma, u, P
+    worst = [0.0] * 5                                # sigma, 1/sigma, u, P, constants
     for T, M, p in _states(2000, 1211):
         ok, *errs = _errors(T, M, p)
         assert ok, (T, M)
         worst = [max(w, e) for w, e in zip(worst, errs)]
     assert worst[0] <= 2.0 ** -40 and worst[3] <= 2.0 ** -40, worst
-    assert worst[1] <= 2.0 ** -38 and worst[2] <= 2.0 ** -38, worst
+    assert worst[1] <= 2.0 ** -38 and worst[2] <= 2.0 ** -38 and worst[4] <= 2.0 ** -38, worst
     # the quantities are not exact (the bound is not vacuous)
     assert min(worst) > 2.0 ** -60, worst
 
 
 def test_fp32_storage_recovery_planted_mistakes_fail():
-    for plant in ("no_newton", "derivative", "constant"):
+    for plant in ("no_newton", "derivative", "constant", "geq0"):
         worst = 0.0
         for T, M, p in _states(200, 7):
-            _, e_sig, _, _, _ = _errors(T, M, p, plant=plant)
-            worst = max(worst, e_sig)
+            _, e_sig, _, _, _, e_c = _errors(T, M, p, plant=plant)
+            worst = max(worst, e_sig, e_c)
         assert worst > 2.0 ** -30, (plant, worst)
 
 
