@@ -373,19 +373,26 @@ __device__ __forceinline__ void quad_lambda(const double* __restrict__ in, int x
   }
 }
 
-// The forward intermediates of the g collide at one node that its reverse step uses
-// (the recovered state of the pulled h, Eq. 10 and the recovery, and the MRT
-// non-equilibrium scalars): 15 values.
+// The forward intermediates of the g collide that a node's reverse step uses; none of
+// them depends on lambda.  Per node: u, sigma, 1/sigma and its square, u^2, kg, g^eq_0
+// minus the rest population, the MRT scalars scaled by the row norms (ne / 2394,
+// np / 252), M, 1 / (6 sqrt(A)), 8 T00, 2 sigma and the odd weights 3 omega w sigma of
+// the axis and diagonal classes (the pulled state, Eq. 10 and the recovery).  Per link
+// pair p, with c = c_p . u and the class weight w: 4.5 w c^2, 3 w c and 2 (4.5 omega w
+// sigma) c, the products that multiply the pair's cotangents.
 struct QFwd {
-  double ux, uy, uz, sigma, is, u2, kg, geq0, ne, np, Mx, My, Mz, rsA, T00;
+  double ux, uy, uz, sigma, is, is2, u2, kg, dg0, ne, np, Mx, My, Mz, rsA6, T8, s2, AA, AD;
 };
-constexpr int kFwdFields = 15;
+constexpr int kFwdFields = 19;
+constexpr int kPairFields = 3;   // per link pair, stored at (3 p + f) n + i
 
-// QFwd from the rest link h0 and lane j's pairs: moments summed over the node's four
-// lanes, then the scalar chain in every lane.
+// QFwd and the pair products of lane j's pairs from the rest link h0 and lane j's
+// pulled pairs: moments summed over the node's four lanes, then the scalar chain in
+// every lane.
 template <bool MRT>
 __device__ __forceinline__ void quad_forward(double h0, const double (&ha)[3], const double (&hb)[3],
-                                             const int (&cd)[3][3], int j, QFwd& F) {
+                                             const int (&cd)[3][3], int j, const StepConst& k, QFwd& F,
+                                             double (&pc)[3][kPairFields]) {
   double Sa = 0, Sd = 0, Mx = 0, My = 0, Mz = 0;
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
@@ -412,84 +419,111 @@ __device__ __forceinline__ void quad_forward(double h0, const double (&ha)[3], c
   const double P = sigma - T00;
   const double u2 = fma(ux, ux, fma(uy, uy, uz * uz));
   const double su2 = sigma * u2, P3 = 3.0 * P;
+  const double geq0 = fma(-0.5, su2, sigma - P3);
   F.kg = fma(-1.5, su2, P3);
-  F.geq0 = fma(-0.5, su2, sigma - P3);
+  F.dg0 = geq0 - h0;
   F.ne = F.np = 0.0;
   if (MRT) {
-    const double n0 = h0 - F.geq0, nA = Sa - P, nD = fma(-0.5, su2, Sd - P);
-    F.ne = fma(8.0, nD, fma(-11.0, nA, -30.0 * n0));
-    F.np = fma(-4.0, nA, fma(12.0, n0, nD));
+    const double n0 = h0 - geq0, nA = Sa - P, nD = fma(-0.5, su2, Sd - P);
+    F.ne = fma(8.0, nD, fma(-11.0, nA, -30.0 * n0)) * (1.0 / 2394.0);
+    F.np = fma(-4.0, nA, fma(12.0, n0, nD)) * (1.0 / 252.0);
   }
   F.ux = ux;
   F.uy = uy;
   F.uz = uz;
   F.sigma = sigma;
   F.is = is;
+  F.is2 = is * is;
   F.u2 = u2;
   F.Mx = Mx;
   F.My = My;
   F.Mz = Mz;
-  F.rsA = rcp_seeded(sA);
-  F.T00 = T00;
+  F.rsA6 = rcp_seeded(sA) * (1.0 / 6.0);
+  F.T8 = 8.0 * T00;
+  F.s2 = 2.0 * sigma;
+  F.AA = k.gA_a * sigma;
+  F.AD = k.gD_a * sigma;
+  const double SA2 = 2.0 * k.gA_s * sigma, SD2 = 2.0 * k.gD_s * sigma;
+  const double wA = 1.0 / 18.0, wD = 1.0 / 36.0;
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    const bool ax = j + 4 * s < 3;
+    const double c = (sel(cd[s][0], ux) + sel(cd[s][1], uy)) + sel(cd[s][2], uz);
+    const double w = ax ? wA : wD;
+    pc[s][0] = (4.5 * w * c) * c;
+    pc[s][1] = (3.0 * w) * c;
+    pc[s][2] = (ax ? SA2 : SD2) * c;
+  }
 }
 
-// Stored QFwd of node i (field q at q * n + i).
+// Stored QFwd of node i (field q at q * n + i) and the pair products (pair p, field f
+// at (kFwdFields + 3 p + f) * n + i).
 __device__ __forceinline__ void store_fwd(double* __restrict__ fw, unsigned long long i, unsigned long long n,
-                                          const QFwd& F) {
-  const double v[kFwdFields] = {F.ux, F.uy, F.uz, F.sigma, F.is, F.u2, F.kg, F.geq0,
-                                F.ne, F.np, F.Mx, F.My, F.Mz, F.rsA, F.T00};
+                                          const QFwd& F, bool node_fields, int j, const double (&pc)[3][kPairFields]) {
+  if (node_fields) {
+    const double v[kFwdFields] = {F.ux, F.uy, F.uz, F.sigma, F.is, F.is2, F.u2, F.kg, F.dg0, F.ne,
+                                  F.np, F.Mx, F.My, F.Mz, F.rsA6, F.T8, F.s2, F.AA, F.AD};
 #pragma unroll
-  for (int q = 0; q < kFwdFields; ++q) fw[q * n + i] = v[q];
+    for (int q = 0; q < kFwdFields; ++q) fw[q * n + i] = v[q];
+  }
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    const int p = j + 4 * s;
+    if (p > 8) continue;
+#pragma unroll
+    for (int f = 0; f < kPairFields; ++f) fw[(kFwdFields + kPairFields * p + f) * n + i] = pc[s][f];
+  }
 }
 __device__ __forceinline__ void load_fwd(const double* __restrict__ fw, unsigned long long i, unsigned long long n,
-                                         QFwd& F) {
+                                         int j, QFwd& F, double (&pc)[3][kPairFields]) {
   double v[kFwdFields];
 #pragma unroll
   for (int q = 0; q < kFwdFields; ++q) v[q] = fw[q * n + i];
-  F.ux = v[0]; F.uy = v[1]; F.uz = v[2]; F.sigma = v[3]; F.is = v[4]; F.u2 = v[5]; F.kg = v[6]; F.geq0 = v[7];
-  F.ne = v[8]; F.np = v[9]; F.Mx = v[10]; F.My = v[11]; F.Mz = v[12]; F.rsA = v[13]; F.T00 = v[14];
+  F.ux = v[0]; F.uy = v[1]; F.uz = v[2]; F.sigma = v[3]; F.is = v[4]; F.is2 = v[5]; F.u2 = v[6]; F.kg = v[7];
+  F.dg0 = v[8]; F.ne = v[9]; F.np = v[10]; F.Mx = v[11]; F.My = v[12]; F.Mz = v[13]; F.rsA6 = v[14]; F.T8 = v[15];
+  F.s2 = v[16]; F.AA = v[17]; F.AD = v[18];
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    const int p = j + 4 * s;
+#pragma unroll
+    for (int f = 0; f < kPairFields; ++f) pc[s][f] = p <= 8 ? fw[(kFwdFields + kPairFields * p + f) * n + i] : 0.0;
+  }
 }
 
 // The reverse of the collide at one node in lane j: per-pair cotangents, sums over the
 // node's four lanes, the scalar chain backwards (MRT scalars, equilibria, recovery,
 // moments), then the stores of mu for lane j's pairs and, in lane 0, the rest link and
-// the omega contributions.
+// the omega contributions.  An FP64 instruction holds its sub-partition's FP64 unit for
+// about 64 cycles whatever its active lanes, so the chain is written for few of them:
+// the forward-only products come stored, the four class sums of the shear/bulk term are
+// combined before the lane sums, and the relaxations fold into fused multiply-adds.
 template <bool MRT>
-__device__ __forceinline__ void quad_backward(const QFwd& F, double h0, double l0, const double (&ha)[3],
-                                              const double (&hb)[3], const double (&la)[3], const double (&lb)[3],
-                                              const int (&cd)[3][3], int j, bool valid, unsigned long long i,
-                                              const StepConst& k, double* __restrict__ mu, double* __restrict__ tb,
-                                              unsigned long long n) {
-  const double ux = F.ux, uy = F.uy, uz = F.uz, sigma = F.sigma, is = F.is;
+__device__ __forceinline__ void quad_backward(const QFwd& F, const double (&pc)[3][kPairFields], double l0,
+                                              const double (&ha)[3], const double (&hb)[3], const double (&la)[3],
+                                              const double (&lb)[3], const int (&cd)[3][3], int j, bool valid,
+                                              unsigned long long i, const StepConst& k, double* __restrict__ mu,
+                                              double* __restrict__ tb, unsigned long long n) {
   const double om = k.omv, om1 = k.omv1;
   const double wA = 1.0 / 18.0, wD = 1.0 / 36.0;
-  const double SA2 = 2.0 * k.gA_s * sigma, SD2 = 2.0 * k.gD_s * sigma, AA = k.gA_a * sigma, AD = k.gD_a * sigma;
-  double SAb = 0, SDb = 0, AAb = 0, ADb = 0, KAb = 0, KDb = 0, wvb = 0, uxb = 0, uyb = 0, uzb = 0;
-  double o1[3], o2[3];
+  double sw = 0, KAb = 0, KDb = 0, wvb = 0, uxb = 0, uyb = 0, uzb = 0;
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
-    const int p = j + 4 * s;
-    const double c = (sel(cd[s][0], ux) + sel(cd[s][1], uy)) + sel(cd[s][2], uz);
-    o1[s] = om1 * la[s];
-    o2[s] = om1 * lb[s];
-    wvb -= ha[s] * la[s] + hb[s] * lb[s];
+    const bool ax = j + 4 * s < 3;   // only slot 0 holds axis pairs; pairs past 8 are zero
+    wvb = fma(-ha[s], la[s], fma(-hb[s], lb[s], wvb));
     const double evb = la[s] + lb[s], odb = la[s] - lb[s];
-    double cub;
-    if (p < 3) {
-      SAb += evb * c * c; KAb += evb; AAb += odb * c;
-      cub = evb * SA2 * c + odb * AA;
-    } else {   // all zero for p > 8
-      SDb += evb * c * c; KDb += evb; ADb += odb * c;
-      cub = evb * SD2 * c + odb * AD;
+    sw = fma(evb, pc[s][0], fma(odb, pc[s][1], sw));
+    if (s == 0) {
+      KAb += ax ? evb : 0.0;
+      KDb += ax ? 0.0 : evb;
+    } else {
+      KDb += evb;
     }
+    const double cub = fma(evb, pc[s][2], odb * (ax ? F.AA : F.AD));
     uxb += sel(cd[s][0], cub);
     uyb += sel(cd[s][1], cub);
     uzb += sel(cd[s][2], cub);
   }
-  SAb = quad_sum(SAb);
-  SDb = quad_sum(SDb);
-  AAb = quad_sum(AAb);
-  ADb = quad_sum(ADb);
+  sw = quad_sum(sw);
   KAb = quad_sum(KAb);
   KDb = quad_sum(KDb);
   wvb = quad_sum(wvb);
@@ -497,27 +531,24 @@ __device__ __forceinline__ void quad_backward(const QFwd& F, double h0, double l
   uyb = quad_sum(uyb);
   uzb = quad_sum(uzb);
   // rest link: out0 = (1 - om) h0 + om geq0 (+ 30 ae - 12 ap)
-  const double o0 = om1 * l0;
-  wvb += (F.geq0 - h0) * l0;
+  wvb = fma(F.dg0, l0, wvb);
   double geq0b = om * l0;
-  double aeb = 30.0 * l0, apb = -12.0 * l0;
-  aeb += 11.0 * KAb - 8.0 * KDb;
-  apb += 4.0 * KAb - KDb;
-  const double kgb = om * (wA * KAb + wD * KDb);
-  wvb += F.kg * (wA * KAb + wD * KDb);
-  const double sw = 4.5 * (wA * SAb + wD * SDb) + 3.0 * (wA * AAb + wD * ADb);
+  const double aeb = fma(11.0, KAb, fma(-8.0, KDb, 30.0 * l0));
+  const double apb = fma(-12.0, l0, fma(4.0, KAb, -KDb));
+  const double t = fma(wA, KAb, wD * KDb);
+  const double kgb = om * t;
+  wvb = fma(F.kg, t, wvb);
   double sigmab = om * sw;
-  wvb += sigma * sw;
+  wvb = fma(F.sigma, sw, wvb);
   double Sab = 0, Sdb = 0, Pb = 0, su2b = 0, h0x = 0, web = 0, wpb = 0;
   if (MRT) {
     const double neb = k.ce * aeb, npb = k.cp * apb;
-    const double ceb = F.ne * aeb * (1.0 / 2394.0), cpb = F.np * apb * (1.0 / 252.0);
-    web = ceb;
-    wpb = cpb;
-    wvb -= ceb + cpb;
-    const double n0b = -30.0 * neb + 12.0 * npb;
-    const double nAb = -11.0 * neb - 4.0 * npb;
-    const double nDb = 8.0 * neb + npb;
+    web = F.ne * aeb;
+    wpb = F.np * apb;
+    wvb = (wvb - web) - wpb;
+    const double n0b = fma(-30.0, neb, 12.0 * npb);
+    const double nAb = fma(-11.0, neb, -4.0 * npb);
+    const double nDb = fma(8.0, neb, npb);
     h0x = n0b;
     geq0b -= n0b;
     Sab = nAb;
@@ -527,25 +558,25 @@ __device__ __forceinline__ void quad_backward(const QFwd& F, double h0, double l
   }
   // geq0 = sigma - P3 - 0.5 su2 ; kg = P3 - 1.5 su2 ; P3 = 3 P ; su2 = sigma u2
   sigmab += geq0b;
-  su2b += -0.5 * geq0b - 1.5 * kgb;
-  Pb += 3.0 * (kgb - geq0b);
-  sigmab += F.u2 * su2b;
-  const double u2b = sigma * su2b;
-  uxb += 2.0 * ux * u2b;
-  uyb += 2.0 * uy * u2b;
-  uzb += 2.0 * uz * u2b;
+  su2b = fma(-0.5, geq0b, fma(-1.5, kgb, su2b));
+  Pb = fma(3.0, kgb - geq0b, Pb);
+  sigmab = fma(F.u2, su2b, sigmab);
+  const double u2b2 = F.s2 * su2b;   // 2 d/du2
+  uxb = fma(F.ux, u2b2, uxb);
+  uyb = fma(F.uy, u2b2, uyb);
+  uzb = fma(F.uz, u2b2, uzb);
   // P = sigma - T00 ; u = M / sigma ; sigma = (2 T00 + sqrt(A)) / 3 ; A = 4 T00^2 - 3 |M|^2
   sigmab += Pb;
   double T00b = -Pb;
-  double Mxb = is * uxb, Myb = is * uyb, Mzb = is * uzb;
-  sigmab -= is * is * (F.Mx * uxb + F.My * uyb + F.Mz * uzb);
-  T00b += (2.0 / 3.0) * sigmab;
-  const double Ab = sigmab * (1.0 / 6.0) * F.rsA;
-  T00b += 8.0 * F.T00 * Ab;
+  double Mxb = F.is * uxb, Myb = F.is * uyb, Mzb = F.is * uzb;
+  sigmab = fma(-F.is2, fma(F.Mx, uxb, fma(F.My, uyb, F.Mz * uzb)), sigmab);
+  T00b = fma(2.0 / 3.0, sigmab, T00b);
+  const double Ab = sigmab * F.rsA6;
+  T00b = fma(F.T8, Ab, T00b);
   const double MMb = -6.0 * Ab;
-  Mxb += F.Mx * MMb;
-  Myb += F.My * MMb;
-  Mzb += F.Mz * MMb;
+  Mxb = fma(F.Mx, MMb, Mxb);
+  Myb = fma(F.My, MMb, Myb);
+  Mzb = fma(F.Mz, MMb, Mzb);
   // T00 = h0 + Sa + Sd
   Sab += T00b;
   Sdb += T00b;
@@ -556,11 +587,11 @@ __device__ __forceinline__ void quad_backward(const QFwd& F, double h0, double l
     if (p > 8) continue;
     const double spb = p < 3 ? Sab : Sdb;
     const double dpb = (sel(cd[s][0], Mxb) + sel(cd[s][1], Myb)) + sel(cd[s][2], Mzb);
-    mu[(unsigned long long)(2 * p + 1) * n + i] = o1[s] + (spb + dpb);
-    mu[(unsigned long long)(2 * p + 2) * n + i] = o2[s] + (spb - dpb);
+    mu[(unsigned long long)(2 * p + 1) * n + i] = fma(om1, la[s], spb + dpb);
+    mu[(unsigned long long)(2 * p + 2) * n + i] = fma(om1, lb[s], spb - dpb);
   }
   if (j == 0) {
-    mu[i] = o0 + (T00b + h0x);
+    mu[i] = fma(om1, l0, T00b + h0x);
     tb[i] += wvb;
     tb[n + i] += web;
     tb[2 * n + i] += wpb;
@@ -569,27 +600,29 @@ __device__ __forceinline__ void quad_backward(const QFwd& F, double h0, double l
 
 // ---- two warp roles (small lattices, the reverse sweep's chain)
 //
-// Nothing in QFwd depends on lambda, only on the forward state, so the reverse step
-// need not recompute it on its own dependent chain.  k_adj_step_ws runs 8 nodes per
-// 64-thread block: warp 0 walks the backward chain of step t from the QFwd stored for
-// step t (fw), and warp 1 computes and stores the QFwd of step t - 1 (from g_prev, the
-// state at step t - 1, into fw_prev) for the next launch.  k_adj_fwd stores the QFwd of
-// one step on its own (the last step, where the reverse sweep starts).
+// Nothing in QFwd or the pair products depends on lambda, only on the forward state,
+// so the reverse step need not compute them on its own dependent chain.  k_adj_step_ws
+// runs 8 nodes per 64-thread block: warp 0 walks the backward chain of step t from the
+// values stored for step t (fw), and warp 1 computes and stores those of step t - 1
+// (from g_prev, the state at step t - 1, into fw_prev) for the next launch.  The two
+// warps run on different sub-partitions, so each has its own FP64 unit.  k_adj_fwd
+// stores the values of one step on its own (the last step, where the sweep starts).
 template <bool MRT, bool TUBE>
-__global__ void __launch_bounds__(64) k_adj_fwd(const double* __restrict__ g, double* __restrict__ fw, AGeo geo) {
+__global__ void __launch_bounds__(64) k_adj_fwd(const double* __restrict__ g, double* __restrict__ fw, AGeo geo,
+                                                StepConst k) {
   const int j = threadIdx.x & 3;
   const int xg = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 2);
   const bool valid = xg < geo.nx;
   const int x = valid ? xg : geo.nx - 1;
   const int y = blockIdx.y, z = blockIdx.z;
   const unsigned long long i = ((unsigned long long)z * geo.ny + y) * geo.nx + x;
-  double ha[3], hb[3];
+  double ha[3], hb[3], pc[3][kPairFields];
   int cd[3][3];
   const double h0 = g[i];
   quad_pull<TUBE>(g, x, y, z, j, geo, ha, hb, cd);
   QFwd F;
-  quad_forward<MRT>(h0, ha, hb, cd, j, F);
-  if (valid && j == 0) store_fwd(fw, i, geo.n, F);
+  quad_forward<MRT>(h0, ha, hb, cd, j, k, F, pc);
+  if (valid) store_fwd(fw, i, geo.n, F, j == 0, j, pc);
 }
 
 template <bool MRT, bool FIRST, bool TUBE>
@@ -603,26 +636,24 @@ __global__ void __launch_bounds__(64) k_adj_step_ws(const double* __restrict__ g
   const int x = valid ? xg : geo.nx - 1;
   const int y = blockIdx.y, z = blockIdx.z;
   const unsigned long long i = ((unsigned long long)z * geo.ny + y) * geo.nx + x;
-  double ha[3], hb[3];
+  double ha[3], hb[3], pc[3][kPairFields];
   int cd[3][3];
+  QFwd F;
   if (threadIdx.x >= 32) {
-    // step t - 1's forward intermediates (none before step 0)
+    // step t - 1's forward values (none before step 0)
     if (g_prev == nullptr) return;
     const double h0 = g_prev[i];
     quad_pull<TUBE>(g_prev, x, y, z, j, geo, ha, hb, cd);
-    QFwd F;
-    quad_forward<MRT>(h0, ha, hb, cd, j, F);
-    if (valid && j == 0) store_fwd(fw_prev, i, geo.n, F);
+    quad_forward<MRT>(h0, ha, hb, cd, j, k, F, pc);
+    if (valid) store_fwd(fw_prev, i, geo.n, F, j == 0, j, pc);
     return;
   }
-  const double h0 = g[i];
   const double l0 = in[i];
   double la[3], lb[3];
   quad_pull<TUBE>(g, x, y, z, j, geo, ha, hb, cd);
   quad_lambda<FIRST, TUBE>(in, x, y, z, j, i, geo, cd, la, lb);
-  QFwd F;
-  load_fwd(fw, i, geo.n, F);
-  quad_backward<MRT>(F, h0, l0, ha, hb, la, lb, cd, j, valid, i, k, mu, tb, geo.n);
+  load_fwd(fw, i, geo.n, j, F, pc);
+  quad_backward<MRT>(F, pc, l0, ha, hb, la, lb, cd, j, valid, i, k, mu, tb, geo.n);
 }
 
 // lambda^T = dJ/dg^T and the per-node misfit.
@@ -827,11 +858,11 @@ cudaError_t enqueue_adjoint(rlb_handle* h, AdjPlan* a, double wP, double wu, boo
     const int t0 = s * K, t1 = std::min(T, t0 + K);
     if (a->quad && t1 == T) {   // the QFwd of the last step
       if (tube) {
-        if (mrt) k_adj_fwd<true, true><<<grid8, 64, 0, st>>>((const double*)b[T - 1 - t0] + 19 * N, a->fw[(T - 1) & 1], geo);
-        else k_adj_fwd<false, true><<<grid8, 64, 0, st>>>((const double*)b[T - 1 - t0] + 19 * N, a->fw[(T - 1) & 1], geo);
+        if (mrt) k_adj_fwd<true, true><<<grid8, 64, 0, st>>>((const double*)b[T - 1 - t0] + 19 * N, a->fw[(T - 1) & 1], geo, h->k);
+        else k_adj_fwd<false, true><<<grid8, 64, 0, st>>>((const double*)b[T - 1 - t0] + 19 * N, a->fw[(T - 1) & 1], geo, h->k);
       } else {
-        if (mrt) k_adj_fwd<true, false><<<grid8, 64, 0, st>>>((const double*)b[T - 1 - t0] + 19 * N, a->fw[(T - 1) & 1], geo);
-        else k_adj_fwd<false, false><<<grid8, 64, 0, st>>>((const double*)b[T - 1 - t0] + 19 * N, a->fw[(T - 1) & 1], geo);
+        if (mrt) k_adj_fwd<true, false><<<grid8, 64, 0, st>>>((const double*)b[T - 1 - t0] + 19 * N, a->fw[(T - 1) & 1], geo, h->k);
+        else k_adj_fwd<false, false><<<grid8, 64, 0, st>>>((const double*)b[T - 1 - t0] + 19 * N, a->fw[(T - 1) & 1], geo, h->k);
       }
       ENQ(cudaGetLastError());
     }
@@ -936,7 +967,8 @@ extern "C" int rlb_adjoint(rlb_handle* h, int nsteps, int checkpoint_every, cons
          plan_alloc(a, (void**)&a->tb, 3 * N * sizeof(double)) && plan_alloc(a, (void**)&a->lossn, N * sizeof(double)) &&
          plan_alloc(a, (void**)&a->sums, 8 * sizeof(double)) && plan_alloc(a, (void**)&a->dde0, N * sizeof(double)) &&
          plan_alloc(a, (void**)&a->tgt, 4 * N * sizeof(double)) && plan_alloc(a, &a->g0copy, state_bytes);
-    for (int i = 0; i < 2 && ok && a->quad; ++i) ok = plan_alloc(a, (void**)&a->fw[i], kFwdFields * N * sizeof(double));
+    for (int i = 0; i < 2 && ok && a->quad; ++i)
+      ok = plan_alloc(a, (void**)&a->fw[i], (kFwdFields + 9 * kPairFields) * N * sizeof(double));
     if (!ok || cudaStreamCreateWithFlags(&a->cap, cudaStreamNonBlocking) != cudaSuccess) {
       free_plan(a);
       return afail(h, RLB_ENOMEM, "cannot allocate adjoint checkpoints and buffers");
