@@ -79,9 +79,9 @@ DEFAULT_STEPS = {"box256": 500, "box128": 500, "box128_fp32": 500, "box512_fp32"
 # 639.4 MB read + 626.3 MB written / 2,097,152; profiles/k_step_box128_f32.md: 318.8 MB
 # read + 268.0 MB written / 2,097,152.
 NCU_BYTES_PER_UPDATE = {"fp64": (639426304 + 626273536) / 2097152, "fp32": (318842112 + 267988736) / 2097152}
-# k_tubes on the 1024-tube sweep at 256 threads x 3 CTAs per SM
-# (profiles/k_tubes_sweep1024_fp32.md): 78.52 GB over 1,719,757 nodes x 200 steps
-NCU_BYTES_PER_UPDATE_TUBES = (33.455014e9 + 45.064466e9) / (1719757 * 200)
+# k_tubes on the 1024-tube sweep at 320 threads x 2 CTAs per SM
+# (profiles/k_tubes_sweep1024_fp32.md): 49.65 GB over 1,719,757 nodes x 200 steps
+NCU_BYTES_PER_UPDATE_TUBES = (12.790533e9 + 36.859571e9) / (1719757 * 200)
 
 # FP64-pipe operations of one FP32-storage node update (the sums are exact on the
 # FP32 and integer pipes and rounded to FP64 by integer bit assembly): recovery 15

@@ -173,14 +173,15 @@ __device__ __forceinline__ void tube_step(int mode, const S* src, S* dst, const 
 // advances it by nsteps: in place pairs of steps on latA (AA scheme), and for an odd
 // nsteps one last two-lattice step into latB.
 // FP32 storage: RLB_TUBES_F32_THREADS threads x RLB_TUBES_F32_BLOCKS CTAs per SM set the
-// register cap (256 x 3: 80 registers, 24 warps per SM); FP64 (the integer-pipe collide
-// needs about 170 registers): up to 256 threads.  The autotuner skips shapes the bound
-// excludes.
+// register cap (320 x 2: 96 registers, none spilled, 20 warps per SM, 304 tubes in
+// flight; 256 x 3 at 80 registers ran 3 % slower: more warps, but 456 tubes overflow
+// L2); FP64 (the integer-pipe collide needs about 170 registers): up to 256 threads.
+// The autotuner skips shapes the bound excludes.
 #ifndef RLB_TUBES_F32_THREADS
-#define RLB_TUBES_F32_THREADS 256
+#define RLB_TUBES_F32_THREADS 320
 #endif
 #ifndef RLB_TUBES_F32_BLOCKS
-#define RLB_TUBES_F32_BLOCKS 3
+#define RLB_TUBES_F32_BLOCKS 2
 #endif
 template <typename S, bool MRT>
 __global__ void __launch_bounds__(sizeof(S) == 8 ? 256 : RLB_TUBES_F32_THREADS, sizeof(S) == 8 ? 1 : RLB_TUBES_F32_BLOCKS) k_tubes(const TubeInfo* __restrict__ order, int ntubes, const StepConst* __restrict__ consts,
@@ -479,7 +480,7 @@ extern "C" int rlb_batch_autotune(rlb_batch* b, int trial_steps, int* chosen) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  const int cand_threads[] = {64, 96, 128, 192, 256, 384, 512};
+  const int cand_threads[] = {64, 96, 128, 160, 192, 224, 256, 288, 320, 352, 384, 448, 512};
   const int cand_ctas[] = {1, 2, 3, 4, 5, 6, 8, 12, 16};
   float best = 1e30f;
   int bt = b->threads, bc = b->ctas_per_sm;
