@@ -164,10 +164,11 @@ __global__ void __launch_bounds__(kBlockX, sizeof(S) == 8 ? RLB_F64_BLOCKS_PER_S
 // registers the single-role kernel needs; out-of-range threads (x >= nx) pull a
 // clamped node, pass the barrier and store nothing.
 // Resident warps per SM the launch bounds ask of the large-lattice blocks (the
-// register cap follows: 32 warps -> 64 registers, a few spilled); small lattices
-// keep 14 64-thread blocks (72 registers).
+// register cap follows: 24 warps -> 80 registers, 40 B spilled; 32 warps -> 64
+// registers, 184 B spilled with the shift-free relaxation, which keeps X^eq live past
+// the product); small lattices keep 14 64-thread blocks.
 #ifndef RLB_WS_WARPS_PER_SM
-#define RLB_WS_WARPS_PER_SM 32
+#define RLB_WS_WARPS_PER_SM 24
 #endif
 // Output rounding route of the f and g warps, one bit per link pair and bit 9 for
 // the rest link: set = FP64-pipe conversion, clear = integer bit assembly with the
@@ -184,7 +185,7 @@ __global__ void __launch_bounds__(kBlockX, sizeof(S) == 8 ? RLB_F64_BLOCKS_PER_S
 #define RLB_WS_WARPS 4
 #endif
 
-template <int W, bool MRT, bool QSEP>
+template <int W, bool MRT, bool QSEP, int RV, int RF>
 __global__ void __launch_bounds__(64 * W, W == 1 ? 14 : RLB_WS_WARPS_PER_SM / (2 * W))
     k_step_ws(const double* __restrict__ src, double* __restrict__ dst, Geo geo, StepConst k,
               unsigned long long* __restrict__ bad) {
@@ -295,7 +296,8 @@ __global__ void __launch_bounds__(64 * W, W == 1 ? 14 : RLB_WS_WARPS_PER_SM / (2
     q.KA = (long long)mulhi((unsigned long long)N0, kEighteenth) - (long long)mulhi((unsigned long long)SX, kThird);
     eq0 = (long long)mulhi((unsigned long long)N0, kThird) - 2 * SX;   // N0/3 - N0 u^2 / 2
   }
-  const unsigned long long Om = is_g ? k.Om_v : k.Om_f;
+  // shift-free relaxation (fx::relax_r): RV / RF = 2 for omega >= 1, 1 below
+  const unsigned long long Om = is_g ? k.Om2_v : k.Om2_f;
   long long c0 = (long long)(Om >> 1), cA = c0, cD = c0;
   long long dq[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   if (MRT && is_g) {
@@ -324,13 +326,13 @@ __global__ void __launch_bounds__(64 * W, W == 1 ? 14 : RLB_WS_WARPS_PER_SM / (2
   if (valid && b) atomicMin(bad, (unsigned long long)node);
   double* out = dst + plane0 + node;
   if (is_g) {
-    const double r0 = from_fixed<(RLB_WS_OUT_G >> 9) & 1>(relax(X[0], eq0, Om, c0), E);
+    const double r0 = from_fixed<(RLB_WS_OUT_G >> 9) & 1>(relax_r<RV>(X[0], eq0, Om, c0), E);
     if (valid) out[0] = r0;
-    relax_links_store<RLB_WS_OUT_G, MRT && QSEP>(X, q, Om, cA, cD, dq, E, out, geo.plane, valid);
+    relax_links_store<RLB_WS_OUT_G, MRT && QSEP, RV>(X, q, Om, cA, cD, dq, E, out, geo.plane, valid);
   } else {
-    const double r0 = from_fixed<(RLB_WS_OUT_F >> 9) & 1>(relax(X[0], eq0, Om, c0), E);
+    const double r0 = from_fixed<(RLB_WS_OUT_F >> 9) & 1>(relax_r<RF>(X[0], eq0, Om, c0), E);
     if (valid) out[0] = r0;
-    relax_links_store<RLB_WS_OUT_F, false>(X, q, Om, cA, cD, dq, E, out, geo.plane, valid);
+    relax_links_store<RLB_WS_OUT_F, false, RF>(X, q, Om, cA, cD, dq, E, out, geo.plane, valid);
   }
 }
 
@@ -353,7 +355,7 @@ __device__ __forceinline__ long long sel3(int j, long long v0, long long v1, lon
   return j == 0 ? v0 : (j == 1 ? v1 : v2);
 }
 
-template <bool MRT>
+template <bool MRT, int RV, int RF>
 __global__ void __launch_bounds__(64, 8) k_step_quad(const double* __restrict__ src, double* __restrict__ dst, Geo geo,
                                                      StepConst k, unsigned long long* __restrict__ bad) {
   using namespace fx;
@@ -491,7 +493,10 @@ __global__ void __launch_bounds__(64, 8) k_step_quad(const double* __restrict__ 
     q.KA = (long long)mulhi((unsigned long long)N0, kEighteenth) - (long long)mulhi((unsigned long long)SX, kThird);
     eq0 = (long long)mulhi((unsigned long long)N0, kThird) - 2 * SX;
   }
-  const unsigned long long Om = is_g ? k.Om_v : k.Om_f;
+  const unsigned long long Om = is_g ? k.Om2_v : k.Om2_f;   // relax_r forms, as in k_step_ws
+  const auto rlx = [is_g](long long X, long long Xeq, unsigned long long O, long long c) {
+    return is_g ? relax_r<RV>(X, Xeq, O, c) : relax_r<RF>(X, Xeq, O, c);
+  };
   long long c0 = (long long)(Om >> 1), cA = c0, cD = c0;
   if (MRT && is_g) {
     const long long n0 = (Xr - eq0) >> 3;
@@ -517,9 +522,9 @@ __global__ void __launch_bounds__(64, 8) k_step_quad(const double* __restrict__ 
     const long long evD = (q.KA >> 1) + ((Xa + Xb) >> 1);
     const long long evP = evD + Yab, odP = (Za + Zb) >> 1;
     const long long evM = evD - Yab, odM = (Za - Zb) >> 1;
-    const long long y0 = relax(X[0], evA + odA, Om, cA), y1 = relax(X[1], evA - odA, Om, cA);
-    const long long y2 = relax(X[2], evP + odP, Om, cD), y3 = relax(X[3], evP - odP, Om, cD);
-    const long long y4 = relax(X[4], evM + odM, Om, cD), y5 = relax(X[5], evM - odM, Om, cD);
+    const long long y0 = rlx(X[0], evA + odA, Om, cA), y1 = rlx(X[1], evA - odA, Om, cA);
+    const long long y2 = rlx(X[2], evP + odP, Om, cD), y3 = rlx(X[3], evP - odP, Om, cD);
+    const long long y4 = rlx(X[4], evM + odM, Om, cD), y5 = rlx(X[5], evM - odM, Om, cD);
     if (valid) {
       out[(unsigned long long)link[0] * geo.plane] = from_fixed_dp(y0, E);
       out[(unsigned long long)link[1] * geo.plane] = from_fixed_dp(y1, E);
@@ -529,7 +534,7 @@ __global__ void __launch_bounds__(64, 8) k_step_quad(const double* __restrict__ 
       out[(unsigned long long)link[5] * geo.plane] = from_fixed_dp(y5, E);
     }
   } else if (valid) {
-    out[0] = from_fixed_dp(relax(X[0], eq0, Om, c0), E);
+    out[0] = from_fixed_dp(rlx(X[0], eq0, Om, c0), E);
   }
 }
 
@@ -680,6 +685,24 @@ bool qsep(const rlb_config& c) {
   return c.collision == RLB_MRT && c.tau_q > 0 && c.tau_q != c.tau_v;
 }
 
+// The FP64 steps for the relaxation forms of omega_v and omega_f (1: omega < 1, 2: omega >= 1).
+template <int W, bool MRT, bool QSEP>
+void launch_ws(int rv, int rf, dim3 grid, cudaStream_t st, const double* s, double* d, const Geo& geo,
+               const StepConst& k, unsigned long long* bad) {
+  if (rv == 2 && rf == 2) k_step_ws<W, MRT, QSEP, 2, 2><<<grid, 64 * W, 0, st>>>(s, d, geo, k, bad);
+  else if (rv == 2) k_step_ws<W, MRT, QSEP, 2, 1><<<grid, 64 * W, 0, st>>>(s, d, geo, k, bad);
+  else if (rf == 2) k_step_ws<W, MRT, QSEP, 1, 2><<<grid, 64 * W, 0, st>>>(s, d, geo, k, bad);
+  else k_step_ws<W, MRT, QSEP, 1, 1><<<grid, 64 * W, 0, st>>>(s, d, geo, k, bad);
+}
+template <bool MRT>
+void launch_quad(int rv, int rf, dim3 grid, cudaStream_t st, const double* s, double* d, const Geo& geo,
+                 const StepConst& k, unsigned long long* bad) {
+  if (rv == 2 && rf == 2) k_step_quad<MRT, 2, 2><<<grid, 64, 0, st>>>(s, d, geo, k, bad);
+  else if (rv == 2) k_step_quad<MRT, 2, 1><<<grid, 64, 0, st>>>(s, d, geo, k, bad);
+  else if (rf == 2) k_step_quad<MRT, 1, 2><<<grid, 64, 0, st>>>(s, d, geo, k, bad);
+  else k_step_quad<MRT, 1, 1><<<grid, 64, 0, st>>>(s, d, geo, k, bad);
+}
+
 template <typename S>
 cudaError_t launch_step(rlb_handle* h, const void* src, void* dst, cudaStream_t st) {
   const Geo geo = make_geo(h);
@@ -726,20 +749,21 @@ cudaError_t launch_step(rlb_handle* h, const void* src, void* dst, cudaStream_t 
     // warp roles: 64-thread blocks (one g and one f warp) for small lattices
     const double* s8 = (const double*)src;
     double* d8 = (double*)dst;
+    const int rv = h->k.r_v, rf = h->k.r_f;
     if (bx == 32 && !q) {
       // four lanes per node: 8 nodes per 64-thread block
       dim3 gq((geo.nx + 7) / 8, geo.ny, geo.nz);
-      if (!mrt) k_step_quad<false><<<gq, 64, 0, st>>>(s8, d8, geo, h->k, h->d_bad);
-      else k_step_quad<true><<<gq, 64, 0, st>>>(s8, d8, geo, h->k, h->d_bad);
+      if (mrt) launch_quad<true>(rv, rf, gq, st, s8, d8, geo, h->k, h->d_bad);
+      else launch_quad<false>(rv, rf, gq, st, s8, d8, geo, h->k, h->d_bad);
     } else if (bx == 32) {
       dim3 gw((geo.nx + 31) / 32, geo.ny, geo.nz);
-      k_step_ws<1, true, true><<<gw, 64, 0, st>>>(s8, d8, geo, h->k, h->d_bad);
+      launch_ws<1, true, true>(rv, rf, gw, st, s8, d8, geo, h->k, h->d_bad);
     } else {
       constexpr int W = RLB_WS_WARPS;
       dim3 gw((geo.nx + 32 * W - 1) / (32 * W), geo.ny, geo.nz);
-      if (!mrt) k_step_ws<W, false, false><<<gw, 64 * W, 0, st>>>(s8, d8, geo, h->k, h->d_bad);
-      else if (!q) k_step_ws<W, true, false><<<gw, 64 * W, 0, st>>>(s8, d8, geo, h->k, h->d_bad);
-      else k_step_ws<W, true, true><<<gw, 64 * W, 0, st>>>(s8, d8, geo, h->k, h->d_bad);
+      if (!mrt) launch_ws<W, false, false>(rv, rf, gw, st, s8, d8, geo, h->k, h->d_bad);
+      else if (!q) launch_ws<W, true, false>(rv, rf, gw, st, s8, d8, geo, h->k, h->d_bad);
+      else launch_ws<W, true, true>(rv, rf, gw, st, s8, d8, geo, h->k, h->d_bad);
     }
     return cudaGetLastError();
   } else {

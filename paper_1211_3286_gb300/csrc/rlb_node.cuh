@@ -88,6 +88,10 @@ struct StepConst {
   // ce * 2^73, cp * 2^69, cq * 2^67 (|ce| < 2/2394, |cp| < 2/252, |cq| < 2/40 keep them
   // below 2^63)
   unsigned long long Om_f, Om_v;
+  // shift-free relaxation (fx::relax_r): r = 2 for omega >= 1 with (omega - 1) 2^64, r = 1
+  // for omega < 1 with omega 2^64 (both even)
+  unsigned long long Om2_f, Om2_v;
+  int r_f, r_v;
   long long CE, CP, CQ;
   // coefficient of the theta term of the C_7 correction (Eq. 38): 1 (Eq. A17) or 2 (as printed)
   double c7_theta;
@@ -134,6 +138,10 @@ inline StepConst make_step_const(double tau_f, double tau_v, double tau_e, doubl
   k.ce_f = (float)k.ce; k.cp_f = (float)k.cp; k.cq_f = (float)k.cq;
   k.Om_f = (unsigned long long)std::ldexp(k.omf, 63) & ~1ull;
   k.Om_v = (unsigned long long)std::ldexp(k.omv, 63) & ~1ull;
+  k.r_f = k.omf >= 1.0 ? 2 : 1;
+  k.r_v = k.omv >= 1.0 ? 2 : 1;
+  k.Om2_f = (unsigned long long)std::ldexp(k.r_f == 2 ? k.omf - 1.0 : k.omf, 64) & ~1ull;
+  k.Om2_v = (unsigned long long)std::ldexp(k.r_v == 2 ? k.omv - 1.0 : k.omv, 64) & ~1ull;
   k.CE = std::llround(std::ldexp(k.ce, 73));
   k.CP = std::llround(std::ldexp(k.cp, 69));
   k.CQ = std::llround(std::ldexp(k.cq, 67));
@@ -652,6 +660,19 @@ __device__ __forceinline__ long long relax(long long X, long long Xeq, unsigned 
   const unsigned long long y = (unsigned long long)(X - Xeq) << 1;
   return X - (long long)mulhi(y ^ kSignBit, Om) + c;
 }
+// The same without the shift, from the base the sign of omega - 1 picks (R = 1: omega < 1,
+// Om2 = omega 2^64, X - omega d; R = 2: omega >= 1, Om2 = (omega - 1) 2^64,
+// X^eq - (omega - 1) d; d = X - X^eq): mulhi(d + 2^63, Om2) is w d + Om2 / 2, and c
+// carries + Om2 / 2.  R = 0 is relax.
+template <int R>
+__device__ __forceinline__ long long relax_r(long long X, long long Xeq, unsigned long long Om, long long c) {
+  if constexpr (R == 0) {
+    return relax(X, Xeq, Om, c);
+  } else {
+    const unsigned long long y = (unsigned long long)(X - Xeq) ^ kSignBit;
+    return (R == 2 ? Xeq : X) - (long long)mulhi(y, Om) + c;
+  }
+}
 // Per-distribution equilibrium pieces on its grid (Eqs. 7-9 split per link pair):
 //   axis pair i:   ev = KA + X_i,                          od = Z_i
 //   diagonal i,j:  ev = KA/2 + (X_i + X_j)/2 +- Y_ij,       od = (Z_i +- Z_j)/2
@@ -709,7 +730,7 @@ __device__ __forceinline__ void relax_links(const long long (&X)[19], const EqPi
 
 // relax_links writing each link straight to out[a * stride] (when st) as soon as it is
 // rounded, so that the results do not all stay live until a final store loop.
-template <int DP, bool ODD>
+template <int DP, bool ODD, int R = 0>
 __device__ __forceinline__ void relax_links_store(const long long (&X)[19], const EqPieces& q, unsigned long long Om,
                                                   long long cA, long long cD, const long long (&dq)[9], int E,
                                                   double* __restrict__ out, unsigned long long stride, bool st) {
@@ -725,8 +746,8 @@ __device__ __forceinline__ void relax_links_store(const long long (&X)[19], cons
   for (int p = 0; p < 9; ++p) {
     const long long c = p < 3 ? cA : cD;
     const long long d = ODD ? dq[p] : 0;
-    const long long ya = relax(X[2 * p + 1], ev[p] + od[p], Om, c + d);
-    const long long yb = relax(X[2 * p + 2], ev[p] - od[p], Om, c - d);
+    const long long ya = relax_r<R>(X[2 * p + 1], ev[p] + od[p], Om, c + d);
+    const long long yb = relax_r<R>(X[2 * p + 2], ev[p] - od[p], Om, c - d);
     const double da = ((DP >> p) & 1) ? from_fixed_dp(ya, E) : from_fixed_pos(ya, E);
     const double db = ((DP >> p) & 1) ? from_fixed_dp(yb, E) : from_fixed_pos(yb, E);
     if (st) {
