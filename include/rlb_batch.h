@@ -72,7 +72,7 @@ int rlb_batch_autotune(rlb_batch* b, int trial_steps, int* chosen);
 
 /* Set the launch shape of later rlb_batch_run calls without timing anything (a shape
  * rlb_batch_autotune chose earlier, say): threads per CTA, a multiple of 32 up to the
- * kernel's launch bound (256 for FP32 storage and for FP64), and CTAs per SM, 1 up to
+ * kernel's launch bound (320 for FP32 storage, 256 for FP64), and CTAs per SM, 1 up to
  * the occupancy limit at that block size (0 = that limit).  RLB_EINVAL (state
  * unchanged) for any other value.  Results do not depend on the shape: each tube is
  * advanced by one CTA and every node's arithmetic is the same. */
