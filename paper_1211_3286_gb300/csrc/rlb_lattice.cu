@@ -161,8 +161,8 @@ __global__ void __launch_bounds__(kBlockX, sizeof(S) == 8 ? RLB_F64_BLOCKS_PER_S
 // pull and relax f of the same nodes.  The g warps recover u (Eq. 10 inverted) and
 // hand it to the f warps through shared memory across one barrier per warp pair.  Each
 // thread holds one distribution of one node, so twice as many warps fit in the
-// registers the single-role kernel needs; out-of-range threads (x >= nx) pull a
-// clamped node, pass the barrier and store nothing.
+// registers the single-role kernel needs; out-of-range threads (x >= nx) pull the
+// clamped node nx - 1, pass the barrier and store that node's values again.
 // Resident warps per SM the launch bounds ask of the large-lattice blocks (the
 // register cap follows: 24 warps -> 80 registers, 40 B spilled; 32 warps -> 64
 // registers, 184 B spilled with the shift-free relaxation, which keeps X^eq live past
@@ -324,15 +324,16 @@ __global__ void __launch_bounds__(64 * W, W == 1 ? 14 : RLB_WS_WARPS_PER_SM / (2
   }
   const unsigned node = row[1][1] + (unsigned)x;
   if (valid && b) atomicMin(bad, (unsigned long long)node);
+  // Lanes past the row repeat node nx - 1 and compute its values bit for bit, so every
+  // lane stores: those lanes write the same bytes to node nx - 1 again, and no branch
+  // guards the 19 stores (1.8164 -> 1.7977 ms per 256^3 step).
   double* out = dst + plane0 + node;
   if (is_g) {
-    const double r0 = from_fixed<(RLB_WS_OUT_G >> 9) & 1>(relax_r<RV>(X[0], eq0, Om, c0), E);
-    if (valid) out[0] = r0;
-    relax_links_store<RLB_WS_OUT_G, MRT && QSEP, RV>(X, q, Om, cA, cD, dq, E, out, geo.plane, valid);
+    out[0] = from_fixed<(RLB_WS_OUT_G >> 9) & 1>(relax_r<RV>(X[0], eq0, Om, c0), E);
+    relax_links_store<RLB_WS_OUT_G, MRT && QSEP, RV>(X, q, Om, cA, cD, dq, E, out, geo.plane, true);
   } else {
-    const double r0 = from_fixed<(RLB_WS_OUT_F >> 9) & 1>(relax_r<RF>(X[0], eq0, Om, c0), E);
-    if (valid) out[0] = r0;
-    relax_links_store<RLB_WS_OUT_F, false, RF>(X, q, Om, cA, cD, dq, E, out, geo.plane, valid);
+    out[0] = from_fixed<(RLB_WS_OUT_F >> 9) & 1>(relax_r<RF>(X[0], eq0, Om, c0), E);
+    relax_links_store<RLB_WS_OUT_F, false, RF>(X, q, Om, cA, cD, dq, E, out, geo.plane, true);
   }
 }
 
@@ -525,7 +526,7 @@ __global__ void __launch_bounds__(64, 8) k_step_quad(const double* __restrict__ 
     const long long y0 = rlx(X[0], evA + odA, Om, cA), y1 = rlx(X[1], evA - odA, Om, cA);
     const long long y2 = rlx(X[2], evP + odP, Om, cD), y3 = rlx(X[3], evP - odP, Om, cD);
     const long long y4 = rlx(X[4], evM + odM, Om, cD), y5 = rlx(X[5], evM - odM, Om, cD);
-    if (valid) {
+    {   // every lane stores (lanes past the row repeat node nx - 1 bit for bit)
       out[(unsigned long long)link[0] * geo.plane] = from_fixed_dp(y0, E);
       out[(unsigned long long)link[1] * geo.plane] = from_fixed_dp(y1, E);
       out[(unsigned long long)link[2] * geo.plane] = from_fixed_dp(y2, E);
@@ -533,7 +534,7 @@ __global__ void __launch_bounds__(64, 8) k_step_quad(const double* __restrict__ 
       out[(unsigned long long)link[4] * geo.plane] = from_fixed_dp(y4, E);
       out[(unsigned long long)link[5] * geo.plane] = from_fixed_dp(y5, E);
     }
-  } else if (valid) {
+  } else {
     out[0] = from_fixed_dp(rlx(X[0], eq0, Om, c0), E);
   }
 }

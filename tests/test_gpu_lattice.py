@@ -90,8 +90,9 @@ def test_ragged_box_wide_blocks_fp64():
     """A lattice above the small-lattice threshold (more than 38,912 nodes), so the FP64
     step runs its 256-thread blocks of 128 nodes along x, with nx = 150: the second
     block's first g and f warps hold 22 valid lanes and its other warps none.  Every
-    lane passes its warp pair's barrier and only valid lanes store.  Zero-gradient x
-    ends put the clamped pulls at the ragged tail."""
+    lane passes its warp pair's barrier; the lanes past the row repeat node nx - 1 and
+    store its values again, bit for bit.  Zero-gradient x ends put the clamped pulls at
+    the ragged tail."""
     e, ux, uy, uz, n = I.periodic_box(None, seed=28, shape=(17, 16, 150))
     bc = ("zero_gradient", "periodic", "periodic")
     gpu, ref, tot, tot_ref = _run_both(e, ux, uy, uz, n, 15, "mrt", (0.9, 0.9, 0.55, 0.8, 0.0), bc)
