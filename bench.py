@@ -76,9 +76,9 @@ DEFAULT_STEPS = {"box256": 500, "box128": 500, "box128_fp32": 500, "box512_fp32"
 # DRAM bytes (read + write) per node update of the step kernel, from ncu captures of the
 # 128^3 box with the same kernel (the 256^3 / 512^3 lattices exceed the capture size
 # rule); traffic per launch = bytes per update x nodes.  profiles/k_step_ws_box128_f64.md:
-# 638.2 MB read + 579.2 MB written / 2,097,152; profiles/k_step_box128_f32.md: 318.8 MB
+# 639.1 MB read + 580.9 MB written / 2,097,152; profiles/k_step_box128_f32.md: 318.8 MB
 # read + 268.0 MB written / 2,097,152.
-NCU_BYTES_PER_UPDATE = {"fp64": (638177792 + 579154944) / 2097152, "fp32": (318842112 + 267988736) / 2097152}
+NCU_BYTES_PER_UPDATE = {"fp64": (639101952 + 580899840) / 2097152, "fp32": (318842112 + 267988736) / 2097152}
 # k_tubes on the 1024-tube sweep at 320 threads x 2 CTAs per SM
 # (profiles/k_tubes_sweep1024_fp32.md): 49.65 GB over 1,719,757 nodes x 200 steps
 NCU_BYTES_PER_UPDATE_TUBES = (12.790533e9 + 36.859571e9) / (1719757 * 200)
