@@ -61,7 +61,9 @@ extern "C" {
                                         (every value on the grid of its node's largest: 2^-56 of it; the
                                         recovery's root and reciprocal to ~2^-58), rounded once to FP64 per
                                         link; the output fields are recovered in FP64 */
-#define RLB_FP32_STORAGE         1   /* populations stored in FP32; sums, recovery, gamma in FP64 */
+#define RLB_FP32_STORAGE         1   /* populations stored in FP32; conservation sums exact, recovery
+                                        in FP64 arithmetic (one Newton step on sigma's quadratic from
+                                        an FP32 seed, ~2^-40), gamma in FP64; per-link work in FP32 */
 #define RLB_CORR_NONE            0
 #define RLB_CORR_C7              1   /* Eq. 37 with C_7 of Eq. 38 on the m_7 = p_xx moment; its theta term
                                         with the coefficient 1 of Eq. A17 */
